@@ -1,0 +1,198 @@
+"""O2 / O4: the level-l approximation of Algorithm 1, literally, in FP64
+(oracle; test infrastructure only).
+
+Steps, in the paper's order and notation (Sec. III-IV):
+
+1. matrix representation of each noise, M_E = sum_k E_k (x) E_k^*  (Sec. III);
+2. tensor permutation M -> M~: with M's edges (1,2) as row and (3,4) as
+   column, M~ takes (1,3) as row and (2,4) as column (Sec. IV, Fig. 3a);
+3. SVD M~ = S D T^dagger with d_0 the largest singular value;
+   U~_i = d_i S|i>, V~_i = T|i>, so M~ = sum_i U~_i V~_i^dagger (Fig. 3b);
+4. tensor permutation back: M = sum_i U_i (x) V_i (Fig. 3c);
+5. Algorithm 1: for every level k <= l, every site set p_1 < ... < p_k and
+   every choice of a non-dominant factor i in {1,2,3} at those sites (the
+   dominant factor U_0 (x) V_0 everywhere else), the double-size network
+   splits into the network on the original wires (gates U, factors U_i) and
+   the one on the conjugate wires (gates U^*, factors V_i); both are
+   contracted -- here by a plain state-vector sweep -- and multiplied;
+   T_k sums those products and A(l) = sum_{k<=l} T_k.
+
+O4 is the canonical list of kept assignments in exactly that loop order
+(level, then site tuple lexicographic, then factor tuple lexicographic),
+packed as 64-bit records: bits 0-3 the level u, then for r = 0..u-1 a 14-bit
+field at bit 4 + 14 r holding the site index (12 bits) and, above it, the
+factor index (2 bits).
+"""
+
+import itertools
+import math
+
+import numpy as np
+
+from . import gates as G
+from . import ir as IR
+from . import statevector as SV
+from .density_matrix import state_from_spec
+
+DOMINANCE_RTOL = 1e-12
+
+
+class NotDominant(ValueError):
+    pass
+
+
+def matrix_representation(kraus):
+    """M_E = sum_k E_k (x) E_k^*  (Sec. III)."""
+    m = np.zeros((4, 4), dtype=np.complex128)
+    for e in kraus:
+        m += np.kron(e, e.conj())
+    return m
+
+
+def tensor_permutation(m):
+    """Regroup a 4x4 matrix with (row edges 1,2 ; column edges 3,4) into
+    (row edges 1,3 ; column edges 2,4)  (Sec. IV, Fig. 3a).  An involution."""
+    t = np.asarray(m).reshape(2, 2, 2, 2)          # [e1, e2, e3, e4]
+    return t.transpose(0, 2, 1, 3).reshape(4, 4)   # [(e1, e3), (e2, e4)]
+
+
+def svd_factors(kraus):
+    """SVD of M~ and the factors of Fig. 3.
+
+    Returns (d, U, V, Ut, Vt): singular values d_0 >= ... >= d_3, 2x2 factors
+    with M_E = sum_i U_i (x) V_i, and the vectors U~_i = d_i S|i>, V~_i = T|i>.
+    Raises NotDominant when d_0 does not strictly exceed d_1 (the dominant
+    factor would not be unique)."""
+    mt = tensor_permutation(matrix_representation(kraus))
+    s, d, th = np.linalg.svd(mt)
+    t = th.conj().T
+    if d[0] - d[1] <= DOMINANCE_RTOL * d[0]:
+        raise NotDominant("largest singular value is not unique")
+    ut = [d[i] * s[:, i] for i in range(4)]
+    vt = [t[:, i] for i in range(4)]
+    # U~_i V~_i^dagger, permuted back, is U_i (x) V_i with
+    # U_i[e1, e3] = U~_i[(e1, e3)] and V_i[e2, e4] = conj(V~_i[(e2, e4)])
+    u = [ut[i].reshape(2, 2) for i in range(4)]
+    v = [vt[i].conj().reshape(2, 2) for i in range(4)]
+    return d, u, v, ut, vt
+
+
+def dominant_and_rest(kraus):
+    """M' = U_0 (x) V_0 and M-bar = sum_{i>=1} U_i (x) V_i (Sec. IV)."""
+    _, u, v, _, _ = svd_factors(kraus)
+    m_dom = np.kron(u[0], v[0])
+    m_rest = sum(np.kron(u[i], v[i]) for i in range(1, 4))
+    return m_dom, m_rest
+
+
+# ----------------------------------------------------------------------------
+# kept assignments (O4)
+
+def kept_assignments(n_noise, level):
+    """(k, sites, factors) in Algorithm 1's loop order."""
+    level = min(level, n_noise)
+    for k in range(level + 1):
+        for sites in itertools.combinations(range(n_noise), k):
+            for idx in itertools.product((1, 2, 3), repeat=k):
+                yield k, sites, idx
+
+
+def pack_record(k, sites, idx):
+    if k > 4:
+        raise ValueError("records hold at most 4 insertions")
+    r = k
+    for j, (s, i) in enumerate(zip(sites, idx)):
+        if s >= 4096:
+            raise ValueError("site index does not fit the 12-bit record field")
+        r |= (s | (i << 12)) << (4 + 14 * j)
+    return r
+
+
+def enumerate_records(n_noise, level):
+    return [pack_record(k, s, i) for k, s, i in kept_assignments(n_noise, level)]
+
+
+def term_count(n_noise, level):
+    level = min(level, n_noise)
+    return sum(math.comb(n_noise, u) * 3 ** u for u in range(level + 1))
+
+
+# ----------------------------------------------------------------------------
+# contraction of one split network by a state-vector sweep
+
+def _network_amplitude(circuit, psi, v, inserted, conjugate_side):
+    """Contract one of the two networks of a substituted double-size network.
+
+    Original side: <v| C[factors] |psi> with the gates U.
+    Conjugate side: <v^*| C^*[factors] |psi^*> with the gates U^* (the lower
+    half of the double-size network of Sec. III)."""
+    n = circuit.n
+    s = psi.conj() if conjugate_side else psi.copy()
+    for kind, idx in IR.events(circuit):
+        if kind == "gate":
+            name, qs, ps = circuit.gates[idx]
+            g = G.gate_matrix(name, ps)
+            s = SV.apply_op(s, n, qs, g.conj() if conjugate_side else g)
+        else:
+            s = SV.apply_1q(s, n, circuit.noises[idx][1], inserted[idx])
+    bra = v.conj() if conjugate_side else v
+    return complex(np.vdot(bra, s))
+
+
+def prepared_factors(circuit):
+    return [svd_factors(k) for (_, _, k) in circuit.noises]
+
+
+def term_value(circuit, psi, v, factors, sites, idx):
+    """X of Algorithm 1 for one kept assignment: the product of the two
+    contracted networks."""
+    n_noise = len(circuit.noises)
+    choice = [0] * n_noise
+    for s, i in zip(sites, idx):
+        choice[s] = i
+    ins_u = [factors[s][1][choice[s]] for s in range(n_noise)]
+    ins_v = [factors[s][2][choice[s]] for s in range(n_noise)]
+    a = _network_amplitude(circuit, psi, v, ins_u, False)
+    b = _network_amplitude(circuit, psi, v, ins_v, True)
+    return a * b
+
+
+def _fsum_complex(xs):
+    return complex(math.fsum(x.real for x in xs), math.fsum(x.imag for x in xs))
+
+
+def approximate(circuit, psi_spec, v_spec, level, keep_terms=False, amplitude_fn=None):
+    """A(l) of Algorithm 1.
+
+    Returns dict(F=complex A(l), T=[complex T_0..T_l], terms=[(record, X)] if
+    keep_terms, n_terms).  Levels above N are clamped to N."""
+    n = circuit.n
+    psi = state_from_spec(psi_spec, n)
+    v = state_from_spec(v_spec, n, circuit, psi)
+    factors = prepared_factors(circuit)
+    n_noise = len(circuit.noises)
+    level = min(level, n_noise)
+    per_level = [[] for _ in range(level + 1)]
+    terms = []
+    for k, sites, idx in kept_assignments(n_noise, level):
+        if amplitude_fn is None:
+            x = term_value(circuit, psi, v, factors, sites, idx)
+        else:
+            x = amplitude_fn(circuit, psi, v, factors, sites, idx)
+        per_level[k].append(x)
+        if keep_terms:
+            terms.append((pack_record(k, sites, idx) if k <= 4 else None, x))
+    t = [_fsum_complex(xs) for xs in per_level]
+    return {"F": _fsum_complex(t), "T": t, "terms": terms,
+            "n_terms": term_count(n_noise, level)}
+
+
+def site_set_sums(terms, n_noise):
+    """Sum of term values per site set (basis independent under degenerate
+    singular values).  terms: [(record, X)]."""
+    out = {}
+    for rec, x in terms:
+        k = rec & 15
+        sites = tuple(((rec >> (4 + 14 * j)) & 0xFFF) for j in range(k))
+        out[sites] = out.get(sites, 0) + x
+    return out
