@@ -1,0 +1,211 @@
+/*
+ * nqs.h -- C ABI of libnqs: level-l SVD noise expansion of a noisy circuit's
+ * fidelity, evaluated by complex64 state-vector sweeps on an sm_103a GPU.
+ *
+ * The quantity (Problem 1, Sec. III): for a noisy circuit E = E_d o ... o E_1
+ * with N single-qubit noise channels, an input |psi> and a test state |v>,
+ *     F = <v| E(|psi><psi|) |v>.
+ * The approximation (Sec. IV, Fig. 3, Algorithm 1): each noise's matrix
+ * representation M = sum_k E_k (x) E_k^* is tensor-permuted, factored by SVD
+ * into M = sum_{i=0..3} U_i (x) V_i with d_0 the dominant singular value, and
+ * A(l) = sum_{u<=l} T_u keeps the assignments with at most l non-dominant
+ * factors.  For a CPTP channel the permuted matrix is Hermitian positive
+ * semidefinite, so U_i = sqrt(d_i) K_i (x) conj(sqrt(d_i) K_i) with one 2x2
+ * K_i per factor and every term is |<v| C[K_sigma] |psi>|^2 >= 0.
+ *
+ * Conventions
+ *   - Qubit q is bit q of a basis index; a state is 2^n complex64 values
+ *     (interleaved float re, im), index = sum_q x_q 2^q.
+ *   - Two-qubit gate matrices are indexed 2*b(first qubit) + b(second qubit).
+ *   - Every function returns NQS_OK (0) or an NQS_ERR_* code and leaves its
+ *     outputs untouched on error, unless stated otherwise.  nqs_strerror gives
+ *     a message.  Device faults detected after a launch are reported as
+ *     NQS_ERR_CUDA.
+ *   - A handle is not thread-safe; distinct handles may be used from
+ *     different threads.  Streams are cudaStream_t passed as void* (NULL =
+ *     the legacy default stream).
+ *   - Device memory is obtained through the allocator installed with
+ *     nqs_set_allocator (default: cudaMalloc / cudaFree) and owned by the
+ *     handle until nqs_destroy.
+ */
+#ifndef NQS_H
+#define NQS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+enum {
+    NQS_OK = 0,
+    NQS_ERR_ARG = 1,            /* invalid argument, size or qubit index */
+    NQS_ERR_PARSE = 2,          /* malformed circuit text */
+    NQS_ERR_NOT_CPTP = 3,       /* ||sum_k E_k^dag E_k - I||_max > 1e-10 */
+    NQS_ERR_NOT_DOMINANT = 4,   /* d_0 - d_1 <= 1e-12 d_0: no unique dominant factor */
+    NQS_ERR_NOMEM = 5,          /* allocator returned NULL */
+    NQS_ERR_CUDA = 6,           /* a CUDA runtime call or kernel launch failed */
+    NQS_ERR_ORDER = 7,          /* call sequence violated (e.g. fidelity before prepare) */
+    NQS_ERR_DEVICE_TIMEOUT = 8, /* a bounded device-side wait gave up (reported in result.status) */
+    NQS_ERR_UNSUPPORTED = 9     /* request outside the supported range (documented per call) */
+};
+
+typedef struct nqs_circuit* nqs_handle;
+
+/* ---- states ------------------------------------------------------------- */
+enum {
+    NQS_STATE_BASIS = 0,   /* |bits> */
+    NQS_STATE_DENSE = 1,   /* caller-owned device buffer of 2^n complex64, read-only,
+                              valid until the stream reaches the end of the call */
+    NQS_STATE_IDEAL = 2    /* only for v: U|psi>, the noiseless circuit applied to psi */
+};
+
+typedef struct {
+    int32_t kind;
+    uint64_t bits;         /* NQS_STATE_BASIS */
+    const void* dev;       /* NQS_STATE_DENSE: device pointer, 16-byte aligned */
+} nqs_state;
+
+/* ---- noise sites -------------------------------------------------------- */
+typedef struct {
+    int32_t after_gate;    /* acts right after this gate index; -1 = before gate 0 */
+    uint32_t qubit;
+    uint32_t n_kraus;      /* 1..16 */
+    const double* kraus;   /* n_kraus x 2x2 complex128, row-major, interleaved re/im:
+                              kraus[8*k + 2*(2*a+b) + {0,1}] = (re, im) of E_k[a][b] */
+} nqs_noise;
+
+enum {
+    NQS_PREP_PRUNE_ZERO_RANK = 1   /* drop factors with d_i < 1e-10 d_0 from the expansion */
+};
+
+/* ---- results ------------------------------------------------------------ */
+#define NQS_MAX_LEVEL 16
+
+typedef struct {
+    double F;                      /* A(l) = sum_{u<=l} T_u (Algorithm 1's Result) */
+    double T[NQS_MAX_LEVEL + 1];   /* T_u, u = 0..level; zero above */
+    double imag_residual;          /* |Im sum X|: 0 for the single-amplitude form */
+    uint64_t n_terms;              /* sum_{u<=l} C(N,u) * (#non-dominant factors)^u */
+    double bound;                  /* per-site truncation bound (see nqs_truncation_bound) */
+    int32_t level;                 /* level after clamping to N */
+    int32_t status;                /* NQS_OK or an asynchronous device error */
+} nqs_result;
+
+/* ---- allocator ---------------------------------------------------------- */
+typedef void* (*nqs_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*nqs_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+
+/* Install the device-memory allocator used by every later allocation of
+ * every handle (process-wide).  Passing NULL for both restores
+ * cudaMalloc/cudaFree.  Memory already held keeps the functions it came from. */
+int nqs_set_allocator(nqs_alloc_fn alloc, nqs_free_fn release, void* ctx);
+
+/* ---- circuit and noise -------------------------------------------------- */
+
+/* Parse the circuit text (gates h x y z t rx ry rz u3 cz cx and optional
+ * noise records; format in the package documentation) into a new handle.
+ * Sec. II: the circuit is the gate sequence U = U_d ... U_1.
+ * Errors: NQS_ERR_ARG (NULL pointers), NQS_ERR_PARSE, NQS_ERR_UNSUPPORTED
+ * (n_qubits outside 1..34). */
+int nqs_load_circuit(const char* ir_text, nqs_handle* out);
+
+/* Factor every noise channel (Sec. IV, Fig. 3): check CPTP, build the
+ * permuted matrix M~ = sum_k vec(E_k) vec(E_k)^dag, diagonalise it in FP64
+ * (Hermitian Jacobi), sort the singular values d_0 >= ... >= d_3, require a
+ * unique dominant value, and keep K_i = sqrt(d_i) reshape(eigenvector_i).
+ * sites == NULL and n_sites == 0 use the noise records of the circuit text;
+ * otherwise `sites` replaces them (ordered by after_gate, stable).  Copies
+ * all inputs.  Errors: NQS_ERR_ARG, NQS_ERR_NOT_CPTP, NQS_ERR_NOT_DOMINANT. */
+int nqs_prepare_noise(nqs_handle h, const nqs_noise* sites, size_t n_sites, uint32_t flags);
+
+/* A(l) for <v| E(|psi><psi|) |v> (Algorithm 1), levels above N clamped to N.
+ * Runs entirely on the GPU in `stream`: a backward sweep from v storing the
+ * states phi_s = (everything after site s)^dag |v>, a forward sweep from psi
+ * reducing <phi_s| K_i |chi_s> at every site, and for l >= 2 depth-first
+ * re-sweeps from each first insertion.  `out` may be device, pinned host or
+ * pageable host memory; it is written with one stream-ordered copy (for
+ * pageable memory the call returns after the copy completed).
+ * Errors: NQS_ERR_ARG (bad state kind, level < 0, level > NQS_MAX_LEVEL after
+ * clamping), NQS_ERR_ORDER (not prepared), NQS_ERR_NOMEM, NQS_ERR_CUDA. */
+int nqs_fidelity(nqs_handle h, const nqs_state* psi, const nqs_state* v, int level,
+                 nqs_result* out, void* stream);
+
+/* Evaluate `count` handles; entry k uses psis[k], vs[k], levels[k] and writes
+ * outs[k].  Same semantics and errors as nqs_fidelity per entry; the first
+ * failing entry's code is returned. */
+int nqs_batch_fidelity(const nqs_handle* hs, size_t count, const nqs_state* psis,
+                       const nqs_state* vs, const int* levels, nqs_result* outs, void* stream);
+
+/* ---- inspection hooks (tests) ------------------------------------------- */
+
+/* Kept assignments of Algorithm 1 in canonical order (level u ascending, site
+ * tuple lexicographic, factor tuple lexicographic over {1,2,3}), packed:
+ * bits 0-3 = u; for r < u the 14-bit field at bit 4+14r holds the site
+ * (low 12 bits) and the factor index (high 2 bits).  Needs level <= 4 and
+ * N <= 4096 (else NQS_ERR_UNSUPPORTED).  *count receives the total; at most
+ * `cap` records are written. */
+int nqs_enumerate_terms(nqs_handle h, int level, uint64_t* rec, size_t cap, size_t* count);
+
+/* Factors of noise site `site` after nqs_prepare_noise: d4[i] = d_i and
+ * K[8*i + 2*(2a+b) + {0,1}] = K_i[a][b] (complex128), K_i = sqrt(d_i) A_i. */
+int nqs_noise_factors(nqs_handle h, uint32_t site, double* d4, double* K);
+
+/* Term values X of the last nqs_fidelity on this handle, in canonical order,
+ * copied to host memory `out` (synchronises the stream of that call). */
+int nqs_term_values(nqs_handle h, double* out, size_t cap, size_t* count);
+
+/* Truncation bound of level l: sum over site sets S with |S| > l of
+ * prod_{s in S} ||M-bar_s|| prod_{s not in S} ||M'_s|| (spectral norms of the
+ * dropped and dominant parts, Theorem 1's argument per site). */
+int nqs_truncation_bound(nqs_handle h, int level, double* out);
+
+typedef struct {
+    int32_t n_qubits;
+    int32_t n_gates;
+    int32_t n_sites;
+    int32_t n_ops;              /* fused operations of the sweep plan */
+    int32_t n_passes;           /* tile passes of one full sweep */
+    int32_t tile_qubits;        /* qubits held in shared memory per tile */
+    uint64_t workspace_bytes;   /* device bytes held by the handle */
+} nqs_info;
+
+int nqs_get_info(nqs_handle h, nqs_info* out);
+
+/* Per-kernel timing of the calls made since profiling was switched on:
+ * CUDA events recorded around every sweep-pass launch on the call's stream.
+ * kind 0 = gate-sweep passes, 1 = finishers/reductions, 2 = other. */
+typedef struct {
+    uint64_t launches;
+    double total_ms;
+    double algorithmic_bytes;   /* sum over launches of 16 B x 2^n x states per pass
+                                   plus 8 B x 2^n per checkpoint read or write */
+} nqs_kernel_stats;
+
+int nqs_set_profiling(nqs_handle h, int on);
+int nqs_get_kernel_stats(nqs_handle h, int kind, nqs_kernel_stats* out);
+
+/* ---- standalone kernels -------------------------------------------------- */
+
+/* Reduced 2x2 matrix of two states on one qubit:
+ *   R[a][b] = sum over all other bits of conj(phi[.., a, ..]) * chi[.., b, ..],
+ * so <phi| K |chi> = sum_ab K[a][b] R[a][b] (the level-1 term of Algorithm 1
+ * read off checkpoints).  phi, chi: device, 2^n complex64, 16-byte aligned.
+ * R_out: 8 doubles (re, im of R00, R01, R10, R11), device or host memory,
+ * written stream-ordered.  scratch: device memory of at least
+ * nqs_reduced_matrix_scratch_bytes(n) bytes (per-block partial sums).
+ * Errors: NQS_ERR_ARG (n outside 1..34, qubit >= n, NULL, small scratch). */
+int nqs_reduced_matrix(const void* phi, const void* chi, int n, int qubit, double* R_out,
+                       void* scratch, size_t scratch_bytes, void* stream);
+size_t nqs_reduced_matrix_scratch_bytes(int n);
+
+void nqs_destroy(nqs_handle h);
+const char* nqs_strerror(int code);
+const char* nqs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NQS_H */

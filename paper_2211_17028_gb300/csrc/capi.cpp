@@ -1,0 +1,314 @@
+// C ABI of libnqs (include/nqs.h): argument validation, handle lifetime, the
+// device allocator hook, and the host-only inspection entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "nqs_internal.h"
+
+namespace nqs {
+
+namespace {
+nqs_alloc_fn g_alloc = nullptr;
+nqs_free_fn g_free = nullptr;
+void* g_ctx = nullptr;
+constexpr int kTileQubits = 12;
+}  // namespace
+
+void* dev_alloc(size_t bytes, void* stream) {
+    if (bytes == 0) bytes = 256;
+    if (g_alloc) return g_alloc(bytes, stream, g_ctx);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(void* p, size_t bytes, void* stream) {
+    if (!p) return;
+    if (g_free) {
+        g_free(p, bytes, stream, g_ctx);
+        return;
+    }
+    cudaFree(p);
+}
+
+int engine_collect_stats(Handle& h);
+
+}  // namespace nqs
+
+using namespace nqs;
+
+extern "C" {
+
+int nqs_set_allocator(nqs_alloc_fn alloc, nqs_free_fn release, void* ctx) {
+    if ((alloc == nullptr) != (release == nullptr)) return NQS_ERR_ARG;
+    g_alloc = alloc;
+    g_free = release;
+    g_ctx = ctx;
+    return NQS_OK;
+}
+
+int nqs_load_circuit(const char* ir_text, nqs_handle* out) {
+    if (!ir_text || !out) return NQS_ERR_ARG;
+    Handle* h = new (std::nothrow) Handle();
+    if (!h) return NQS_ERR_NOMEM;
+    std::string err;
+    int rc = parse_circuit(ir_text, h->circ, err);
+    if (rc != NQS_OK) {
+        delete h;
+        return rc;
+    }
+    *out = reinterpret_cast<nqs_handle>(h);
+    return NQS_OK;
+}
+
+int nqs_prepare_noise(nqs_handle hh, const nqs_noise* sites, size_t n_sites, uint32_t flags) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return NQS_ERR_ARG;
+    if ((sites == nullptr) != (n_sites == 0)) return NQS_ERR_ARG;
+    if (flags & ~(uint32_t)NQS_PREP_PRUNE_ZERO_RANK) return NQS_ERR_ARG;
+    std::vector<NoiseSite> ns;
+    if (sites) {
+        if (n_sites > 4096) return NQS_ERR_UNSUPPORTED;
+        int prev = -2;
+        for (size_t i = 0; i < n_sites; ++i) {
+            const nqs_noise& s = sites[i];
+            if (s.qubit >= (uint32_t)h->circ.n || s.n_kraus < 1 || s.n_kraus > 16 || !s.kraus) return NQS_ERR_ARG;
+            if (s.after_gate < -1 || s.after_gate >= (int)h->circ.gates.size() || s.after_gate < prev)
+                return NQS_ERR_ARG;
+            prev = s.after_gate;
+            NoiseSite t;
+            t.after_gate = s.after_gate;
+            t.qubit = (int)s.qubit;
+            for (uint32_t k = 0; k < s.n_kraus; ++k) {
+                Mat2 m;
+                for (int e = 0; e < 4; ++e) m[e] = cd(s.kraus[8 * k + 2 * e], s.kraus[8 * k + 2 * e + 1]);
+                t.kraus.push_back(m);
+            }
+            ns.push_back(t);
+        }
+    } else {
+        ns = h->circ.noises;
+    }
+    std::vector<Factors> fac(ns.size());
+    for (size_t i = 0; i < ns.size(); ++i) {
+        int rc = factor_noise(ns[i], (flags & NQS_PREP_PRUNE_ZERO_RANK) != 0, fac[i]);
+        if (rc != NQS_OK) return rc;
+    }
+    engine_destroy(*h);
+    h->circ.noises = ns;
+    h->factors = fac;
+    build_plan(h->circ, h->factors, kTileQubits, h->plan);
+    h->prepared = true;
+    return NQS_OK;
+}
+
+static int check_state(const Handle& h, const nqs_state* s, bool allow_ideal) {
+    if (!s) return NQS_ERR_ARG;
+    if (s->kind == NQS_STATE_BASIS) {
+        if (h.circ.n < 64 && (s->bits >> h.circ.n) != 0) return NQS_ERR_ARG;
+        return NQS_OK;
+    }
+    if (s->kind == NQS_STATE_DENSE) {
+        if (!s->dev || ((uintptr_t)s->dev & 15u)) return NQS_ERR_ARG;
+        return NQS_OK;
+    }
+    if (s->kind == NQS_STATE_IDEAL && allow_ideal) return NQS_OK;
+    return NQS_ERR_ARG;
+}
+
+int nqs_fidelity(nqs_handle hh, const nqs_state* psi, const nqs_state* v, int level, nqs_result* out,
+                 void* stream) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !out || level < 0) return NQS_ERR_ARG;
+    if (!h->prepared) return NQS_ERR_ORDER;
+    int rc = check_state(*h, psi, false);
+    if (rc) return rc;
+    rc = check_state(*h, v, true);
+    if (rc) return rc;
+    int lvl = std::min(level, (int)h->factors.size());
+    if (lvl > NQS_MAX_LEVEL) return NQS_ERR_ARG;
+    return engine_fidelity(*h, psi, v, lvl, out, stream);
+}
+
+int nqs_batch_fidelity(const nqs_handle* hs, size_t count, const nqs_state* psis, const nqs_state* vs,
+                       const int* levels, nqs_result* outs, void* stream) {
+    if (count == 0) return NQS_OK;
+    if (!hs || !psis || !vs || !levels || !outs) return NQS_ERR_ARG;
+    for (size_t i = 0; i < count; ++i) {
+        int rc = nqs_fidelity(hs[i], &psis[i], &vs[i], levels[i], &outs[i], stream);
+        if (rc != NQS_OK) return rc;
+    }
+    return NQS_OK;
+}
+
+int nqs_enumerate_terms(nqs_handle hh, int level, uint64_t* rec, size_t cap, size_t* count) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !count || level < 0 || (cap && !rec)) return NQS_ERR_ARG;
+    if (!h->prepared) return NQS_ERR_ORDER;
+    const int N = (int)h->factors.size();
+    int lvl = std::min(level, N);
+    if (lvl > 4 || N > 4096) return NQS_ERR_UNSUPPORTED;
+    size_t written = 0, total = 0;
+    auto emit = [&](uint64_t r) {
+        if (written < cap) rec[written++] = r;
+        ++total;
+    };
+    for (int u = 0; u <= lvl; ++u) {
+        std::vector<int> comb(u);
+        for (int j = 0; j < u; ++j) comb[j] = j;
+        while (true) {
+            // factor tuples over each chosen site's kept factors, lexicographic
+            std::vector<int> fp(u, 0);
+            bool any = true;
+            for (int j = 0; j < u; ++j)
+                if (h->factors[comb[j]].m == 0) any = false;
+            while (any) {
+                uint64_t r = (uint64_t)u;
+                for (int j = 0; j < u; ++j) {
+                    uint64_t field = (uint64_t)comb[j] | ((uint64_t)h->factors[comb[j]].keep[fp[j]] << 12);
+                    r |= field << (4 + 14 * j);
+                }
+                emit(r);
+                int j = u - 1;
+                while (j >= 0 && fp[j] + 1 >= h->factors[comb[j]].m) fp[j--] = 0;
+                if (j < 0) break;
+                ++fp[j];
+            }
+            if (u == 0) break;
+            int j = u - 1;
+            while (j >= 0 && comb[j] == N - u + j) --j;
+            if (j < 0) break;
+            ++comb[j];
+            for (int t = j + 1; t < u; ++t) comb[t] = comb[t - 1] + 1;
+        }
+    }
+    *count = total;
+    return NQS_OK;
+}
+
+int nqs_noise_factors(nqs_handle hh, uint32_t site, double* d4, double* K) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !d4 || !K) return NQS_ERR_ARG;
+    if (!h->prepared) return NQS_ERR_ORDER;
+    if (site >= h->factors.size()) return NQS_ERR_ARG;
+    const Factors& f = h->factors[site];
+    for (int i = 0; i < 4; ++i) {
+        d4[i] = f.d[i];
+        for (int e = 0; e < 4; ++e) {
+            K[8 * i + 2 * e] = f.K[i][e].real();
+            K[8 * i + 2 * e + 1] = f.K[i][e].imag();
+        }
+    }
+    return NQS_OK;
+}
+
+int nqs_term_values(nqs_handle hh, double* out, size_t cap, size_t* count) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !count || (cap && !out)) return NQS_ERR_ARG;
+    return engine_term_values(*h, out, cap, count);
+}
+
+int nqs_truncation_bound(nqs_handle hh, int level, double* out) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !out || level < 0) return NQS_ERR_ARG;
+    if (!h->prepared) return NQS_ERR_ORDER;
+    std::vector<double> poly(1, 1.0);
+    for (const auto& f : h->factors) {
+        std::vector<double> nx(poly.size() + 1, 0.0);
+        for (size_t i = 0; i < poly.size(); ++i) {
+            nx[i] += poly[i] * f.norm_dom;
+            nx[i + 1] += poly[i] * f.norm_rest;
+        }
+        poly.swap(nx);
+    }
+    double b = 0.0;
+    for (size_t i = (size_t)level + 1; i < poly.size(); ++i) b += poly[i];
+    *out = b;
+    return NQS_OK;
+}
+
+int nqs_get_info(nqs_handle hh, nqs_info* out) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !out) return NQS_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->n_qubits = h->circ.n;
+    out->n_gates = (int32_t)h->circ.gates.size();
+    out->n_sites = (int32_t)h->circ.noises.size();
+    if (h->prepared) {
+        out->n_ops = (int32_t)h->plan.ops.size();
+        out->n_passes = (int32_t)h->plan.free_passes.size();
+        out->tile_qubits = h->plan.k;
+    }
+    out->workspace_bytes = engine_workspace_bytes(*h);
+    return NQS_OK;
+}
+
+int nqs_set_profiling(nqs_handle hh, int on) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return NQS_ERR_ARG;
+    if (h->profiling) {
+        int rc = engine_collect_stats(*h);
+        if (rc) return rc;
+    }
+    h->profiling = on != 0;
+    if (on)
+        for (auto& s : h->stats) s = nqs_kernel_stats{};
+    return NQS_OK;
+}
+
+int nqs_get_kernel_stats(nqs_handle hh, int kind, nqs_kernel_stats* out) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !out || kind < 0 || kind > 2) return NQS_ERR_ARG;
+    if (h->profiling) {
+        int rc = engine_collect_stats(*h);
+        if (rc) return rc;
+    }
+    *out = h->stats[kind];
+    return NQS_OK;
+}
+
+int nqs_reduced_matrix(const void* phi, const void* chi, int n, int qubit, double* R_out, void* scratch,
+                       size_t scratch_bytes, void* stream) {
+    if (!phi || !chi || !R_out || !scratch || n < 1 || n > 34 || qubit < 0 || qubit >= n) return NQS_ERR_ARG;
+    if (((uintptr_t)phi & 15u) || ((uintptr_t)chi & 15u) || ((uintptr_t)scratch & 7u)) return NQS_ERR_ARG;
+    return engine_reduced_matrix(phi, chi, n, qubit, R_out, scratch, scratch_bytes, stream);
+}
+
+size_t nqs_reduced_matrix_scratch_bytes(int n) {
+    if (n < 1 || n > 34) return 0;
+    return engine_reduced_matrix_scratch_bytes(n);
+}
+
+void nqs_destroy(nqs_handle hh) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return;
+    engine_destroy(*h);
+    delete h;
+}
+
+const char* nqs_strerror(int code) {
+    switch (code) {
+        case NQS_OK: return "ok";
+        case NQS_ERR_ARG: return "invalid argument";
+        case NQS_ERR_PARSE: return "malformed circuit text";
+        case NQS_ERR_NOT_CPTP: return "noise channel is not trace preserving (||sum E^dag E - I|| > 1e-10)";
+        case NQS_ERR_NOT_DOMINANT: return "noise channel has no unique dominant singular value";
+        case NQS_ERR_NOMEM: return "device allocation failed";
+        case NQS_ERR_CUDA: return "CUDA runtime error";
+        case NQS_ERR_ORDER: return "call order violated (prepare the noise first)";
+        case NQS_ERR_DEVICE_TIMEOUT: return "a bounded device-side wait gave up";
+        case NQS_ERR_UNSUPPORTED: return "request outside the supported range";
+        default: return "unknown status";
+    }
+}
+
+const char* nqs_version(void) { return "nqs 0.1 (sm_103a)"; }
+
+}  // extern "C"

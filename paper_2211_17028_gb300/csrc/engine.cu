@@ -1,0 +1,1301 @@
+// Sweep engine: complex64 state-vector passes on sm_103a and the schedule
+// that turns them into the level-l expansion of Algorithm 1 (Sec. IV).
+//
+// Every kept term of the expansion is X = |<v| C[K_sigma] |psi>|^2, where
+// C[K_sigma] is the noiseless gate sequence with the 2x2 factor K_{sigma_s}
+// inserted at each noise site s (K_0 = dominant factor).  Instead of one
+// contraction per term, the engine
+//   1. sweeps v backwards (adjoint operations, K_0^dagger at sites) and stores
+//      phi_s = (operations after site s)^dagger |v> at every site;
+//   2. sweeps psi forwards; at site s the state is chi_s and the 2x2 reduced
+//      matrix R_s[a][b] = sum_rest conj(phi_s[rest,a]) chi_s[rest,b] gives
+//      every level-1 amplitude <phi_s| K_i |chi_s> = sum_ab K_i[a][b] R_s[a][b]
+//      (and, with K_0, the level-0 amplitude);
+//   3. for level >= 2 spawns w_i = K_i chi_s at each site and re-sweeps the
+//      three branch states from there, reducing against phi_t at every later
+//      site t, recursing depth first up to the level.
+// A pass holds 2^k amplitudes of each state in shared memory (the tile's
+// qubits are the low c qubits plus those the pass acts on), applies a run of
+// fused operations and writes the tile back; site operations inside a pass
+// read phi_t straight from HBM, write checkpoints and spawned states, and
+// accumulate reductions in FP32 per thread, FP32 per warp (shuffle), then FP64
+// per warp slot in shared memory; per-block partials are summed in a fixed
+// order by a finisher, so results are bit-reproducible.  Terms are summed
+// per level with Neumaier compensation in canonical order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "nqs_internal.h"
+
+namespace nqs {
+
+constexpr int kMaxTileQ = 12;          // 4096 amplitudes = 32 KB per state tile
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxEvents = 8;          // reductions per pass (planner cuts passes accordingly)
+constexpr int kMaxQ = 34;
+
+enum : int {
+    FL_REDUCE = 1,
+    FL_SPAWN = 2,
+    FL_SAVE = 4,
+    FL_APPLY = 8,     // apply the site's K (K_0, or K_0^dagger backwards) after the other actions
+    FL_KDIAG = 32
+};
+
+struct DevOp {
+    int type;      // OP_*
+    int a, b;      // tile positions of q0, q1 (-1 when outside the tile)
+    int qa, qb;    // qubits
+    int mat;       // offset (in float2) of the matrix in the matrix table
+    int site;
+    int flags;     // site flags | event << 8 | spawn count << 16
+};
+
+struct PassArgs {
+    const DevOp* ops;
+    int n_ops;
+    const float2* mats;
+    int n, k, c;
+    int n_events;
+    int local[kMaxTileQ];
+    int nonlocal[kMaxQ];
+    long long n_tiles;
+    const float2* in[3];
+    float2* out[3];
+    float2* const* ckpt;   // phi_s slots
+    float2* spawn[9];
+    double* partials;      // [(event * S + state) * grid + block][8]
+};
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {   // a*b + c
+    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ int insert0(int p, int pos) {
+    return ((p >> pos) << (pos + 1)) | (p & ((1 << pos) - 1));
+}
+
+template <int S>
+struct PassShared {
+    unsigned long long hi_off[1 << (kMaxTileQ - 5)];
+    double acc[kMaxEvents][S][kWarps][8];
+};
+
+template <int S>
+__global__ void __launch_bounds__(kThreads) pass_kernel(const PassArgs P) {
+    extern __shared__ __align__(16) float2 tile[];   // S * 2^k
+    __shared__ PassShared<S> sh;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int k = P.k, c = P.c;
+    const int T = 1 << k;
+    const int cmask = (1 << c) - 1;
+    const int nhi = 1 << (k - c);
+
+    for (int h = tid; h < nhi; h += kThreads) {
+        unsigned long long off = 0;
+        for (int j = 0; j < k - c; ++j)
+            if ((h >> j) & 1) off |= 1ull << P.local[c + j];
+        sh.hi_off[h] = off;
+    }
+    for (int i = tid; i < kMaxEvents * S * kWarps * 8; i += kThreads) (&sh.acc[0][0][0][0])[i] = 0.0;
+    __syncthreads();
+
+    for (long long t = blockIdx.x; t < P.n_tiles; t += gridDim.x) {
+        unsigned long long base = 0;
+        for (int j = 0; j < P.n - k; ++j)
+            if ((t >> j) & 1) base |= 1ull << P.nonlocal[j];
+        auto gaddr = [&](int j) -> unsigned long long { return base | sh.hi_off[j >> c] | (unsigned long long)(j & cmask); };
+
+        // load (2 amplitudes per 16-byte vector; j even so the address is aligned)
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const float4* src = reinterpret_cast<const float4*>(P.in[s]);
+            for (int f = tid; f < (T >> 1); f += kThreads) {
+                int j = f << 1;
+                float4 v = __ldcs(src + (gaddr(j) >> 1));
+                tile[s * T + j] = make_float2(v.x, v.y);
+                tile[s * T + j + 1] = make_float2(v.z, v.w);
+            }
+        }
+        __syncthreads();
+
+        for (int o = 0; o < P.n_ops; ++o) {
+            const DevOp op = P.ops[o];
+            if (op.type == OP_G1) {
+                const float2 m0 = P.mats[op.mat], m1 = P.mats[op.mat + 1];
+                const float2 m2 = P.mats[op.mat + 2], m3 = P.mats[op.mat + 3];
+                const int bit = 1 << op.a;
+                for (int p = tid; p < (T >> 1); p += kThreads) {
+                    int j0 = insert0(p, op.a), j1 = j0 | bit;
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+                        float2 x0 = tile[s * T + j0], x1 = tile[s * T + j1];
+                        tile[s * T + j0] = cfma(m0, x0, cmul(m1, x1));
+                        tile[s * T + j1] = cfma(m2, x0, cmul(m3, x1));
+                    }
+                }
+            } else if (op.type == OP_G2) {
+                float2 m[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) m[e] = P.mats[op.mat + e];
+                const int lo = min(op.a, op.b), hi = max(op.a, op.b);
+                const int ba = 1 << op.a, bb = 1 << op.b;
+                for (int p = tid; p < (T >> 2); p += kThreads) {
+                    int j = insert0(insert0(p, lo), hi);
+                    int idx[4] = {j, j | bb, j | ba, j | ba | bb};
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+                        float2 x[4];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) x[r] = tile[s * T + idx[r]];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            float2 y = cmul(m[4 * r], x[0]);
+                            y = cfma(m[4 * r + 1], x[1], y);
+                            y = cfma(m[4 * r + 2], x[2], y);
+                            y = cfma(m[4 * r + 3], x[3], y);
+                            tile[s * T + idx[r]] = y;
+                        }
+                    }
+                }
+            } else if (op.type == OP_D1) {
+                const float2 d0 = P.mats[op.mat], d1 = P.mats[op.mat + 3];
+                if (op.a >= 0) {
+                    for (int j = tid; j < T; j += kThreads) {
+                        float2 d = ((j >> op.a) & 1) ? d1 : d0;
+#pragma unroll
+                        for (int s = 0; s < S; ++s) tile[s * T + j] = cmul(d, tile[s * T + j]);
+                    }
+                } else {
+                    float2 d = ((base >> op.qa) & 1) ? d1 : d0;
+                    for (int j = tid; j < T; j += kThreads)
+#pragma unroll
+                        for (int s = 0; s < S; ++s) tile[s * T + j] = cmul(d, tile[s * T + j]);
+                }
+            } else if (op.type == OP_D2) {
+                float2 d[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) d[e] = P.mats[op.mat + 5 * e];
+                const int fa = (op.a < 0) ? (int)((base >> op.qa) & 1) : -1;
+                const int fb = (op.b < 0) ? (int)((base >> op.qb) & 1) : -1;
+                for (int j = tid; j < T; j += kThreads) {
+                    int b0 = fa >= 0 ? fa : ((j >> op.a) & 1);
+                    int b1 = fb >= 0 ? fb : ((j >> op.b) & 1);
+                    float2 f = d[2 * b0 + b1];
+#pragma unroll
+                    for (int s = 0; s < S; ++s) tile[s * T + j] = cmul(f, tile[s * T + j]);
+                }
+            } else if (op.type == OP_SITE) {
+                const int fl = op.flags & 0xff;
+                const int ev = (op.flags >> 8) & 0xff;
+                const int nspawn = (op.flags >> 16) & 0xff;
+                const int bit = 1 << op.a;
+                const float2 k0 = P.mats[op.mat], k1 = P.mats[op.mat + 1];
+                const float2 k2 = P.mats[op.mat + 2], k3 = P.mats[op.mat + 3];
+                const float2* phi = (fl & FL_REDUCE) ? P.ckpt[op.site] : nullptr;
+                float2* save = (fl & FL_SAVE) ? P.ckpt[op.site] : nullptr;
+                float r[S][8];
+#pragma unroll
+                for (int s = 0; s < S; ++s)
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) r[s][e] = 0.f;
+                for (int p = tid; p < (T >> 1); p += kThreads) {
+                    int j0 = insert0(p, op.a), j1 = j0 | bit;
+                    unsigned long long g0 = gaddr(j0), g1 = gaddr(j1);
+                    float2 f0, f1;
+                    if (fl & FL_REDUCE) {
+                        f0 = __ldcs(phi + g0);
+                        f1 = __ldcs(phi + g1);
+                    }
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+                        float2 x0 = tile[s * T + j0], x1 = tile[s * T + j1];
+                        // phi_s excludes the site's own factor: save before applying K_0^dagger
+                        if ((fl & FL_SAVE) && s == 0) {
+                            __stcs(save + g0, x0);
+                            __stcs(save + g1, x1);
+                        }
+                        if (fl & FL_REDUCE) {
+                            // R[a][b] += conj(phi_a) * x_b
+                            r[s][0] += f0.x * x0.x + f0.y * x0.y;  r[s][1] += f0.x * x0.y - f0.y * x0.x;
+                            r[s][2] += f0.x * x1.x + f0.y * x1.y;  r[s][3] += f0.x * x1.y - f0.y * x1.x;
+                            r[s][4] += f1.x * x0.x + f1.y * x0.y;  r[s][5] += f1.x * x0.y - f1.y * x0.x;
+                            r[s][6] += f1.x * x1.x + f1.y * x1.y;  r[s][7] += f1.x * x1.y - f1.y * x1.x;
+                        }
+                        if (fl & FL_SPAWN) {
+                            for (int i = 0; i < nspawn; ++i) {
+                                const float2* K = P.mats + op.mat + 4 * (i + 1);
+                                float2* dst = P.spawn[s * 3 + i];
+                                __stcs(dst + g0, cfma(K[0], x0, cmul(K[1], x1)));
+                                __stcs(dst + g1, cfma(K[2], x0, cmul(K[3], x1)));
+                            }
+                        }
+                        if (fl & FL_APPLY) {
+                            float2 y0, y1;
+                            if (fl & FL_KDIAG) {
+                                y0 = cmul(k0, x0);
+                                y1 = cmul(k3, x1);
+                            } else {
+                                y0 = cfma(k0, x0, cmul(k1, x1));
+                                y1 = cfma(k2, x0, cmul(k3, x1));
+                            }
+                            tile[s * T + j0] = y0;
+                            tile[s * T + j1] = y1;
+                        }
+                    }
+                }
+                if (fl & FL_REDUCE) {
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            float v = r[s][e];
+#pragma unroll
+                            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                            if (lane == 0) sh.acc[ev][s][warp][e] += (double)v;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            float4* dst = reinterpret_cast<float4*>(P.out[s]);
+            for (int f = tid; f < (T >> 1); f += kThreads) {
+                int j = f << 1;
+                float2 a = tile[s * T + j], b = tile[s * T + j + 1];
+                __stcs(dst + (gaddr(j) >> 1), make_float4(a.x, a.y, b.x, b.y));
+            }
+        }
+        __syncthreads();
+    }
+
+    for (int i = tid; i < P.n_events * S * 8; i += kThreads) {
+        int e = i & 7, s = (i >> 3) % S, ev = (i >> 3) / S;
+        double v = 0.0;
+        for (int w = 0; w < kWarps; ++w) v += sh.acc[ev][s][w][e];
+        P.partials[((size_t)(ev * S + s) * gridDim.x + blockIdx.x) * 8 + e] = v;
+    }
+}
+
+// Standalone reduced-matrix kernel (nqs_reduced_matrix and the N = 0 path):
+// grid-stride over amplitude pairs of qubit q.
+__global__ void __launch_bounds__(kThreads) reduce2x2_kernel(const float2* __restrict__ phi,
+                                                             const float2* __restrict__ chi, int n, int q,
+                                                             double* __restrict__ partials) {
+    __shared__ double acc[kWarps][8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < kWarps * 8) (&acc[0][0])[tid] = 0.0;
+    __syncthreads();
+    const long long npairs = 1ll << (n - 1);
+    const long long bit = 1ll << q;
+    const long long stride = (long long)gridDim.x * kThreads;
+    long long p = (long long)blockIdx.x * kThreads + tid;
+    while (__any_sync(0xffffffffu, p < npairs)) {
+        float r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int it = 0; it < 16 && p < npairs; ++it, p += stride) {
+            long long lo = p & (bit - 1);
+            long long i0 = ((p - lo) << 1) | lo, i1 = i0 | bit;
+            float2 f0 = __ldcs(phi + i0), f1 = __ldcs(phi + i1);
+            float2 x0 = __ldcs(chi + i0), x1 = __ldcs(chi + i1);
+            r[0] += f0.x * x0.x + f0.y * x0.y;  r[1] += f0.x * x0.y - f0.y * x0.x;
+            r[2] += f0.x * x1.x + f0.y * x1.y;  r[3] += f0.x * x1.y - f0.y * x1.x;
+            r[4] += f1.x * x0.x + f1.y * x0.y;  r[5] += f1.x * x0.y - f1.y * x0.x;
+            r[6] += f1.x * x1.x + f1.y * x1.y;  r[7] += f1.x * x1.y - f1.y * x1.x;
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            float v = r[e];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0) acc[warp][e] += (double)v;
+        }
+    }
+    __syncthreads();
+    if (tid < 8) {
+        double v = 0.0;
+        for (int w = 0; w < kWarps; ++w) v += acc[w][tid];
+        partials[(size_t)blockIdx.x * 8 + tid] = v;
+    }
+}
+
+// Sum per-block partials of one reduction slot in a fixed order: thread t
+// takes blocks t, t+256, ...; then a fixed tree.
+__device__ void sum_partials(const double* part, int grid, double* R, double* scratch) {
+    const int tid = threadIdx.x;
+    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = tid; b < grid; b += kThreads)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] += part[(size_t)b * 8 + e];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) scratch[e * kThreads + tid] = v[e];
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if (tid < w)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) scratch[e * kThreads + tid] += scratch[e * kThreads + tid + w];
+        __syncthreads();
+    }
+    if (tid < 8) R[tid] = scratch[tid * kThreads];
+    __syncthreads();
+}
+
+struct FinishDesc {
+    long long rank;   // -1: no term
+    int kmat;         // offset (doubles) of the 2x2 complex128 factor
+    int pad;
+};
+
+// One block per reduction slot (event, state): R from the partials, then
+// X = |sum_ab K[a][b] R[a][b]|^2 for each factor of the slot.
+__global__ void __launch_bounds__(kThreads) finish_kernel(const double* __restrict__ partials, int grid,
+                                                          const FinishDesc* __restrict__ desc,
+                                                          const double* __restrict__ kmats,
+                                                          double* __restrict__ term_vals) {
+    __shared__ double scratch[8 * kThreads];
+    __shared__ double R[8];
+    sum_partials(partials + (size_t)blockIdx.x * grid * 8, grid, R, scratch);
+    if (threadIdx.x < 4) {
+        FinishDesc d = desc[blockIdx.x * 4 + threadIdx.x];
+        if (d.rank >= 0) {
+            const double* K = kmats + d.kmat;
+            double re = 0, im = 0;
+            for (int e = 0; e < 4; ++e) {
+                double kr = K[2 * e], ki = K[2 * e + 1], rr = R[2 * e], ri = R[2 * e + 1];
+                re += kr * rr - ki * ri;
+                im += kr * ri + ki * rr;
+            }
+            term_vals[d.rank] = re * re + im * im;
+        }
+    }
+}
+
+// One block: fixed-order sum of per-block partials into 8 doubles.
+__global__ void __launch_bounds__(kThreads) partials_sum_kernel(const double* __restrict__ part, int grid,
+                                                                double* __restrict__ R) {
+    __shared__ double scratch[8 * kThreads];
+    __shared__ double r[8];
+    sum_partials(part, grid, r, scratch);
+    if (threadIdx.x < 8) R[threadIdx.x] = r[threadIdx.x];
+}
+
+// Neumaier-compensated per-level sums in canonical order, one block.
+__global__ void __launch_bounds__(kThreads) level_sum_kernel(const double* __restrict__ vals,
+                                                             const long long* __restrict__ level_off, int level,
+                                                             nqs_result* __restrict__ res, double bound,
+                                                             long long n_terms) {
+    __shared__ double s_sum[kThreads], s_comp[kThreads];
+    __shared__ double T[NQS_MAX_LEVEL + 1];
+    const int tid = threadIdx.x;
+    for (int u = 0; u <= level; ++u) {
+        long long lo = level_off[u], hi = level_off[u + 1];
+        long long len = hi - lo;
+        long long chunk = (len + kThreads - 1) / kThreads;
+        long long a = lo + chunk * tid, b = min(hi, a + chunk);
+        double sum = 0.0, comp = 0.0;
+        for (long long i = a; i < b; ++i) {
+            double x = vals[i];
+            double t = sum + x;
+            if (fabs(sum) >= fabs(x)) comp += (sum - t) + x;
+            else comp += (x - t) + sum;
+            sum = t;
+        }
+        s_sum[tid] = sum;
+        s_comp[tid] = comp;
+        __syncthreads();
+        if (tid == 0) {
+            double S = 0.0, C = 0.0;
+            for (int i = 0; i < kThreads; ++i) {
+                double x = s_sum[i];
+                double t = S + x;
+                if (fabs(S) >= fabs(x)) C += (S - t) + x;
+                else C += (x - t) + S;
+                S = t;
+                C += s_comp[i];
+            }
+            T[u] = S + C;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        double S = 0.0, C = 0.0;
+        for (int u = 0; u <= NQS_MAX_LEVEL; ++u) {
+            double x = (u <= level) ? T[u] : 0.0;
+            res->T[u] = x;
+            double t = S + x;
+            if (fabs(S) >= fabs(x)) C += (S - t) + x;
+            else C += (x - t) + S;
+            S = t;
+        }
+        res->F = S + C;
+        res->imag_residual = 0.0;
+        res->n_terms = (uint64_t)n_terms;
+        res->bound = bound;
+        res->level = level;
+        res->status = NQS_OK;
+    }
+}
+
+__global__ void basis_fill_kernel(float2* out, long long dim, unsigned long long bits) {
+    long long stride = (long long)gridDim.x * blockDim.x;
+    float4* o4 = reinterpret_cast<float4*>(out);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (dim >> 1); i += stride) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((unsigned long long)(2 * i) == bits) v.x = 1.f;
+        if ((unsigned long long)(2 * i + 1) == bits) v.z = 1.f;
+        o4[i] = v;
+    }
+}
+
+// ------------------------------------------------------------------ host side
+namespace {
+
+struct RunPass {
+    int op_off = 0, n_ops = 0;       // in the device op buffer
+    int k = 0, c = 0;
+    int local[kMaxTileQ] = {};
+    int nonlocal[kMaxQ] = {};
+    std::vector<int> lin;            // linear op index of each device op
+    std::vector<int> ev_site;        // site of reduction event e
+    int spawn_site = -1;             // site that spawns in this pass (at most one)
+};
+
+struct Run {
+    std::vector<RunPass> passes;     // in execution order
+};
+
+enum LaunchKind { L_PASS, L_FINISH, L_FILL, L_COPY, L_REDUCE2, L_SUM };
+
+struct Launch {
+    LaunchKind kind;
+    int S = 1;
+    PassArgs args{};
+    int op_index = 0;                // offset of the first device op (rebased onto the device table)
+    int grid = 0;
+    size_t smem = 0;
+    // finisher
+    int n_red = 0, fin_grid = 0;
+    size_t desc_off = 0;
+    // fill / copy
+    float2* dst = nullptr;
+    const float2* src = nullptr;
+    unsigned long long bits = 0;
+    double bytes = 0;                // algorithmic bytes (pass kernels)
+};
+
+int blocks_per_sm(int S, size_t smem);
+
+}  // namespace
+
+struct Engine {
+    int sm_count = 0;
+    int device = -1;
+    // persistent device buffers
+    void* buf = nullptr;             // one allocation for states
+    size_t buf_bytes = 0;
+    void* aux = nullptr;             // ops, mats, tables, partials, term values, result
+    size_t aux_bytes = 0;
+    // schedule cache key
+    int level = -1, psi_kind = -1, v_kind = -1;
+    unsigned long long psi_bits = 0, v_bits = 0;
+    const void* psi_dev = nullptr;
+    const void* v_dev = nullptr;
+    std::vector<Launch> launches;
+    double bound = 0;
+    long long n_terms = 0;
+    int eff_level = 0;
+    long long* level_off_dev = nullptr;
+    double* term_vals = nullptr;
+    nqs_result* res_dev = nullptr;
+    FinishDesc* desc_dev = nullptr;
+    double* partials = nullptr;
+    double* kmats_dev = nullptr;
+    // profiling
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+    std::vector<std::pair<int, double>> ev_used;    // kind, bytes per used pair
+    size_t ev_next = 0;
+    cudaStream_t last_stream = nullptr;
+    bool has_result = false;
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? NQS_OK : NQS_ERR_CUDA; }
+
+template <int S>
+void set_smem_attr() {
+    static bool done = false;
+    if (!done) {
+        cudaFuncSetAttribute(pass_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             S * (1 << kMaxTileQ) * (int)sizeof(float2));
+        done = true;
+    }
+}
+
+int blocks_per_sm(int S, size_t smem) {
+    int nb = 0;
+    if (S == 1) {
+        set_smem_attr<1>();
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<1>, kThreads, smem);
+    } else if (S == 2) {
+        set_smem_attr<2>();
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<2>, kThreads, smem);
+    } else {
+        set_smem_attr<3>();
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<3>, kThreads, smem);
+    }
+    return std::max(nb, 1);
+}
+
+// Matrix table builder (float2 for sweeps, complex128 for finishers).
+struct Tables {
+    std::vector<float2> mats;
+    std::vector<double> kmats;     // per site: K_0..K_3, 8 doubles each
+    int add(const cd* m, int cnt, bool adjoint, int dim) {
+        int off = (int)mats.size();
+        for (int r = 0; r < dim; ++r)
+            for (int c = 0; c < dim; ++c) {
+                cd v = adjoint ? std::conj(m[dim * c + r]) : m[dim * r + c];
+                mats.push_back(make_float2((float)v.real(), (float)v.imag()));
+            }
+        (void)cnt;
+        return off;
+    }
+};
+
+enum RunType { RT_IDEAL, RT_BWD, RT_FWD };
+
+// Build device ops for one run type over a segmentation.
+Run make_run(const Plan& plan, const std::vector<PassSpec>& segs, RunType rt, bool reduce, bool spawn,
+             bool level0_only, const std::vector<Factors>& fac, Tables& tab, std::vector<DevOp>& dops) {
+    Run run;
+    std::vector<int> fwd_mat(plan.ops.size(), -1), bwd_mat(plan.ops.size(), -1);
+    for (size_t i = 0; i < plan.ops.size(); ++i) {
+        const HostOp& o = plan.ops[i];
+        int dim = (o.type == OP_G2 || o.type == OP_D2) ? 4 : 2;
+        if (rt == RT_BWD) {
+            bwd_mat[i] = tab.add(o.m.data(), dim * dim, true, dim);
+        } else if (o.type == OP_SITE) {
+            // K_0 followed by the kept non-dominant factors
+            fwd_mat[i] = tab.add(o.m.data(), 4, false, 2);
+            const Factors& f = fac[o.site];
+            for (int j = 0; j < 3; ++j) {
+                Mat2 z{};
+                const Mat2& K = (j < f.m) ? f.K[f.keep[j]] : z;
+                tab.add(K.data(), 4, false, 2);
+            }
+        } else {
+            fwd_mat[i] = tab.add(o.m.data(), dim * dim, false, dim);
+        }
+    }
+    int first_site_done = 0;
+    auto build_pass = [&](const PassSpec& ps, bool reversed) {
+        RunPass rp;
+        rp.k = plan.k;
+        rp.c = plan.c;
+        std::vector<int> pos(plan.n, -1);
+        for (int j = 0; j < plan.k; ++j) {
+            rp.local[j] = ps.local[j];
+            pos[ps.local[j]] = j;
+        }
+        int nl = 0;
+        for (int q = 0; q < plan.n; ++q)
+            if (pos[q] < 0) rp.nonlocal[nl++] = q;
+        rp.op_off = (int)dops.size();
+        auto emit = [&](int i) {
+            const HostOp& o = plan.ops[i];
+            DevOp d{};
+            d.type = o.type;
+            d.qa = o.q0;
+            d.qb = o.q1;
+            d.a = o.q0 >= 0 ? pos[o.q0] : -1;
+            d.b = o.q1 >= 0 ? pos[o.q1] : -1;
+            d.site = o.site;
+            d.mat = (rt == RT_BWD) ? bwd_mat[i] : fwd_mat[i];
+            if (o.type == OP_SITE) {
+                int fl = 0;
+                if (rt == RT_IDEAL) {
+                    return;   // noiseless sweep: sites are absent
+                } else if (rt == RT_BWD) {
+                    fl = FL_APPLY | FL_SAVE;
+                } else {
+                    fl = FL_APPLY;
+                    bool red = reduce && (!level0_only || first_site_done == 0);
+                    if (red) {
+                        fl |= FL_REDUCE | ((int)rp.ev_site.size() << 8);
+                        rp.ev_site.push_back(o.site);
+                    }
+                    if (spawn && fac[o.site].m > 0) {
+                        fl |= FL_SPAWN | (fac[o.site].m << 16);
+                        rp.spawn_site = o.site;
+                    }
+                    first_site_done = 1;
+                }
+                if (o.diag) fl |= FL_KDIAG;
+                d.flags = fl;
+            }
+            dops.push_back(d);
+            rp.lin.push_back(i);
+        };
+        if (!reversed)
+            for (int i = ps.op_begin; i < ps.op_end; ++i) emit(i);
+        else
+            for (int i = ps.op_end - 1; i >= ps.op_begin; --i) emit(i);
+        rp.n_ops = (int)dops.size() - rp.op_off;
+        return rp;
+    };
+    if (rt == RT_BWD) {
+        for (int p = (int)segs.size() - 1; p >= 0; --p) run.passes.push_back(build_pass(segs[p], true));
+    } else {
+        for (const auto& ps : segs) run.passes.push_back(build_pass(ps, false));
+    }
+    return run;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ schedule
+namespace {
+
+struct Builder {
+    Handle& h;
+    Engine& E;
+    const Plan& plan;
+    int level;
+    TermIndex ti;
+    Tables tab;
+    std::vector<DevOp> dops;
+    std::vector<FinishDesc> descs;
+    std::vector<Launch> L;
+    size_t partial_doubles = 0;
+    long long dim;
+    // device buffers (resolved after allocation)
+    float2* main_buf = nullptr;
+    std::vector<float2*> phi;
+    std::vector<std::vector<float2*>> group_bufs;   // per depth (1..level-1)
+    float2** ckpt_dev = nullptr;
+    Run run_ideal, run_bwd;
+    std::vector<Run> run_fwd;    // per depth
+
+    Builder(Handle& hh, Engine& ee, int lvl) : h(hh), E(ee), plan(hh.plan), level(lvl) {
+        dim = 1ll << plan.n;
+    }
+
+    int grid_for(int S, long long tiles) {
+        size_t smem = (size_t)S * (1 << plan.k) * sizeof(float2);
+        long long g = (long long)blocks_per_sm(S, smem) * E.sm_count;
+        return (int)std::max<long long>(1, std::min<long long>(g, tiles));
+    }
+
+    PassArgs pass_args(const RunPass& rp, int start, int S) {
+        PassArgs a{};
+        a.ops = nullptr;
+        a.n_ops = rp.n_ops - start;
+        a.mats = nullptr;
+        a.n = plan.n;
+        a.k = rp.k;
+        a.c = rp.c;
+        a.n_events = (int)rp.ev_site.size();
+        for (int j = 0; j < kMaxTileQ; ++j) a.local[j] = rp.local[j];
+        for (int j = 0; j < kMaxQ; ++j) a.nonlocal[j] = rp.nonlocal[j];
+        a.n_tiles = 1ll << (plan.n - rp.k);
+        a.ckpt = ckpt_dev;
+        return a;
+    }
+
+    void add_pass(const RunPass& rp, int start, int S, const float2* const* in, float2* const* out,
+                  float2* const* spawn, int n_spawn) {
+        if (rp.n_ops - start <= 0 && in[0] == out[0]) return;
+        Launch l;
+        l.kind = L_PASS;
+        l.S = S;
+        l.args = pass_args(rp, start, S);
+        l.op_index = rp.op_off + start;
+        for (int s = 0; s < S; ++s) {
+            l.args.in[s] = in[s];
+            l.args.out[s] = out[s];
+        }
+        for (int i = 0; i < n_spawn; ++i) l.args.spawn[i] = spawn[i];
+        l.grid = grid_for(S, l.args.n_tiles);
+        l.smem = (size_t)S * (1 << plan.k) * sizeof(float2);
+        partial_doubles = std::max(partial_doubles, (size_t)std::max(1, l.args.n_events) * S * l.grid * 8);
+        // algorithmic bytes: state load + store, phi reads, checkpoint and spawn writes
+        double b = 16.0 * dim * S;
+        int n_red = 0, n_save = 0, n_sp = 0;
+        for (int o = start; o < rp.n_ops; ++o) {
+            const DevOp& d = dops[rp.op_off + o];
+            if (d.type != OP_SITE) continue;
+            if (d.flags & FL_REDUCE) ++n_red;
+            if (d.flags & FL_SAVE) ++n_save;
+            if (d.flags & FL_SPAWN) n_sp += (d.flags >> 16) & 0xff;
+        }
+        b += 8.0 * dim * (n_red + n_save + (double)n_sp * S);
+        l.bytes = b;
+        L.push_back(l);
+    }
+
+    // finisher for the last pass launch: slot (event e, state s) -> term ranks
+    template <typename RankFn>
+    void add_finish(const RunPass& rp, int start, int S, RankFn rank_of) {
+        const Launch& pl = L.back();
+        int n_ev = (int)rp.ev_site.size();
+        if (n_ev == 0) return;
+        // events executed in this launch
+        std::vector<char> executed(n_ev, 0);
+        for (int o = start; o < rp.n_ops; ++o) {
+            const DevOp& d = dops[rp.op_off + o];
+            if (d.type == OP_SITE && (d.flags & FL_REDUCE)) executed[(d.flags >> 8) & 0xff] = 1;
+        }
+        Launch f;
+        f.kind = L_FINISH;
+        f.n_red = n_ev * S;
+        f.fin_grid = pl.grid;
+        f.desc_off = descs.size();
+        for (int e = 0; e < n_ev; ++e)
+            for (int s = 0; s < S; ++s)
+                for (int i = 0; i < 4; ++i) {
+                    FinishDesc d{-1, 0, 0};
+                    if (executed[e]) rank_of(rp.ev_site[e], s, i, d);
+                    descs.push_back(d);
+                }
+        L.push_back(f);
+    }
+
+    int kmat_off(int site, int factor) { return site * 32 + factor * 8; }
+
+    // Group of S sibling states spawned at site `s_last` (state s carries the
+    // s-th kept factor there); `prefix` holds the earlier insertions.  The
+    // group sweeps from the operation after the site to the end of the
+    // circuit, reducing against phi_t at every later site t; when the level
+    // allows, it spawns children at each site into the next depth's buffers
+    // (3 per state) and recurses depth first.
+    void dfs_group(int depth, const std::vector<std::pair<int, int>>& prefix, int s_last, int S,
+                   const std::vector<float2*>& bufs) {
+        const Run& run = run_fwd[depth];
+        int pos = plan.site_pos[s_last];
+        int pi = -1, start = 0;
+        for (size_t p = 0; p < run.passes.size() && pi < 0; ++p) {
+            const RunPass& rp = run.passes[p];
+            for (int o = 0; o < rp.n_ops; ++o)
+                if (rp.lin[o] > pos) {
+                    pi = (int)p;
+                    start = o;
+                    break;
+                }
+        }
+        if (pi < 0) {
+            // nothing after the site: the branch states are final, nothing to reduce
+            return;
+        }
+        const bool can_spawn = depth + 1 < (int)group_bufs.size();
+        for (size_t p = pi; p < run.passes.size(); ++p) {
+            const RunPass& rp = run.passes[p];
+            int st = (p == (size_t)pi) ? start : 0;
+            bool spawns = can_spawn && rp.spawn_site >= 0 && rp.lin.size() > 0;
+            // a spawn before `st` (partial first pass) does not execute
+            if (spawns) {
+                int sp_pos = plan.site_pos[rp.spawn_site];
+                if (sp_pos <= pos) spawns = false;
+            }
+            std::vector<float2*> child;
+            if (spawns)
+                for (int i = 0; i < S * 3; ++i) child.push_back(group_bufs[depth + 1][i]);
+            add_pass(rp, st, S, (const float2* const*)bufs.data(), bufs.data(),
+                     child.empty() ? nullptr : child.data(), (int)child.size());
+            add_finish(rp, st, S, [&](int t, int s, int i, FinishDesc& d) {
+                const Factors& ft = h.factors[t];
+                if (i == 0 || i > ft.m || depth + 1 > level) return;
+                std::vector<std::pair<int, int>> terms = prefix;
+                terms.push_back({s_last, s});
+                terms.push_back({t, i - 1});
+                std::sort(terms.begin(), terms.end());
+                int sites[NQS_MAX_LEVEL + 1], fp[NQS_MAX_LEVEL + 1];
+                for (size_t j = 0; j < terms.size(); ++j) {
+                    sites[j] = terms[j].first;
+                    fp[j] = terms[j].second;
+                }
+                d.rank = (long long)ti.rank((int)terms.size(), sites, fp);
+                d.kmat = kmat_off(t, ft.keep[i - 1]);
+            });
+            if (spawns) {
+                int t = rp.spawn_site;
+                for (int s = 0; s < S; ++s) {
+                    std::vector<std::pair<int, int>> pre = prefix;
+                    pre.push_back({s_last, s});
+                    std::vector<float2*> cb(group_bufs[depth + 1].begin() + 3 * s,
+                                            group_bufs[depth + 1].begin() + 3 * s + 3);
+                    dfs_group(depth + 1, pre, t, h.factors[t].m, cb);
+                }
+            }
+        }
+    }
+};
+
+}  // namespace
+
+static int engine_init(Engine& E) {
+    if (E.device >= 0) return NQS_OK;
+    int dev;
+    if (cudaGetDevice(&dev) != cudaSuccess) return NQS_ERR_CUDA;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return NQS_ERR_CUDA;
+    E.device = dev;
+    E.sm_count = prop.multiProcessorCount;
+    return NQS_OK;
+}
+
+static void engine_release(Engine& E, void* stream) {
+    if (E.buf) dev_free(E.buf, E.buf_bytes, stream);
+    if (E.aux) dev_free(E.aux, E.aux_bytes, stream);
+    E.buf = E.aux = nullptr;
+    E.buf_bytes = E.aux_bytes = 0;
+    E.level = -1;
+    E.launches.clear();
+}
+
+// Build (or reuse) the schedule for this level and state kinds.
+static int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* v, int level,
+                          void* stream) {
+    const Plan& plan = h.plan;
+    const int N = (int)h.factors.size();
+    if (E.level == level && E.psi_kind == psi->kind && E.v_kind == v->kind && E.psi_bits == psi->bits &&
+        E.v_bits == v->bits && E.psi_dev == psi->dev && E.v_dev == v->dev)
+        return NQS_OK;
+    engine_release(E, stream);
+
+    Builder B(h, E, level);
+    std::vector<int> m(N);
+    for (int s = 0; s < N; ++s) m[s] = h.factors[s].m;
+    B.ti.build(m, level);
+
+    // runs
+    bool need_ideal = v->kind == NQS_STATE_IDEAL;
+    if (need_ideal) B.run_ideal = make_run(plan, plan.free_passes, RT_IDEAL, false, false, false, h.factors, B.tab, B.dops);
+    if (N > 0) B.run_bwd = make_run(plan, plan.free_passes, RT_BWD, false, false, false, h.factors, B.tab, B.dops);
+    // forward runs per depth d: reduce if d+1 <= level (or level 0 at depth 0), spawn if d+2 <= level
+    int depths = std::max(1, level);
+    for (int d = 0; d < depths; ++d) {
+        bool spawn = d + 2 <= level;
+        bool reduce = (level == 0) ? (d == 0) : (d + 1 <= level);
+        B.run_fwd.push_back(make_run(plan, spawn ? plan.sitecut_passes : plan.free_passes, RT_FWD, reduce && N > 0,
+                                     spawn, level == 0, h.factors, B.tab, B.dops));
+    }
+    // finisher factor table (complex128)
+    B.tab.kmats.assign((size_t)std::max(N, 1) * 32, 0.0);
+    for (int s = 0; s < N; ++s)
+        for (int i = 0; i < 4; ++i)
+            for (int e = 0; e < 4; ++e) {
+                B.tab.kmats[s * 32 + i * 8 + 2 * e] = h.factors[s].K[i][e].real();
+                B.tab.kmats[s * 32 + i * 8 + 2 * e + 1] = h.factors[s].K[i][e].imag();
+            }
+    if (N == 0) {   // identity "factor" for the plain inner product
+        B.tab.kmats[0] = 1.0;
+        B.tab.kmats[6] = 1.0;
+    }
+
+    // state buffers: phi slots, main, group buffers (3 at depth 1, 9 deeper)
+    const size_t sbytes = (size_t)B.dim * sizeof(float2);
+    int n_phi = std::max(N, 1);
+    int n_group = 0;
+    for (int d = 1; d < level; ++d) n_group += (d == 1) ? 3 : 9;
+    size_t n_states = (size_t)n_phi + 1 + n_group;
+    E.buf_bytes = n_states * sbytes;
+    E.buf = dev_alloc(E.buf_bytes, stream);
+    if (!E.buf) {
+        E.buf_bytes = 0;
+        return NQS_ERR_NOMEM;
+    }
+    float2* base = (float2*)E.buf;
+    for (int s = 0; s < n_phi; ++s) B.phi.push_back(base + (size_t)s * B.dim);
+    B.main_buf = base + (size_t)n_phi * B.dim;
+    B.group_bufs.assign(std::max(1, level), {});
+    size_t next = (size_t)n_phi + 1;
+    for (int d = 1; d < level; ++d) {
+        int cnt = (d == 1) ? 3 : 9;
+        for (int i = 0; i < cnt; ++i) B.group_bufs[d].push_back(base + (next++) * B.dim);
+    }
+
+    // --- schedule (device pointers to aux tables are patched after layout) ---
+    // Aux layout is decided after the launches are known; PassArgs hold
+    // offsets relative to placeholder pointers that are rebased below.
+    B.ckpt_dev = nullptr;
+    float2* mainb = B.main_buf;
+    const float2* in1[3];
+    float2* out1[3];
+
+    auto init_state = [&](const nqs_state* st, float2* dst, bool& external, const float2*& ext) {
+        external = false;
+        if (st->kind == NQS_STATE_BASIS) {
+            Launch l;
+            l.kind = L_FILL;
+            l.dst = dst;
+            l.bits = st->bits;
+            B.L.push_back(l);
+        } else {
+            external = true;
+            ext = (const float2*)st->dev;
+        }
+    };
+
+    // 1. v (into main), optionally the ideal sweep, then the backward sweep
+    if (N > 0 || true) {
+        bool ext = false;
+        const float2* ext_ptr = nullptr;
+        if (v->kind == NQS_STATE_IDEAL) {
+            bool pe = false;
+            const float2* pp = nullptr;
+            init_state(psi, mainb, pe, pp);
+            for (size_t p = 0; p < B.run_ideal.passes.size(); ++p) {
+                in1[0] = (p == 0 && pe) ? pp : mainb;
+                out1[0] = mainb;
+                B.add_pass(B.run_ideal.passes[p], 0, 1, in1, out1, nullptr, 0);
+            }
+            if (B.run_ideal.passes.empty() && pe) {
+                Launch l;
+                l.kind = L_COPY;
+                l.dst = mainb;
+                l.src = pp;
+                B.L.push_back(l);
+            }
+        } else {
+            init_state(v, mainb, ext, ext_ptr);
+        }
+        if (N > 0) {
+            for (size_t p = 0; p < B.run_bwd.passes.size(); ++p) {
+                in1[0] = (p == 0 && ext) ? ext_ptr : mainb;
+                out1[0] = mainb;
+                B.add_pass(B.run_bwd.passes[p], 0, 1, in1, out1, nullptr, 0);
+            }
+        } else {
+            // N = 0: keep v in the single phi slot for the final inner product
+            Launch l;
+            l.kind = L_COPY;
+            l.dst = B.phi[0];
+            l.src = ext ? ext_ptr : mainb;
+            B.L.push_back(l);
+        }
+    }
+    // 2. forward sweep from psi, level 0 / 1 reductions, spawns
+    {
+        bool ext = false;
+        const float2* ext_ptr = nullptr;
+        init_state(psi, mainb, ext, ext_ptr);
+        const Run& run = B.run_fwd[0];
+        bool first_red = true;
+        for (size_t p = 0; p < run.passes.size(); ++p) {
+            const RunPass& rp = run.passes[p];
+            in1[0] = (p == 0 && ext) ? ext_ptr : mainb;
+            out1[0] = mainb;
+            std::vector<float2*> sp;
+            if (level >= 2 && rp.spawn_site >= 0)
+                for (int i = 0; i < 3; ++i) sp.push_back(B.group_bufs[1][i]);
+            B.add_pass(rp, 0, 1, in1, out1, sp.empty() ? nullptr : sp.data(), (int)sp.size());
+            B.add_finish(rp, 0, 1, [&](int t, int s, int i, FinishDesc& d) {
+                (void)s;
+                const Factors& ft = h.factors[t];
+                if (i == 0) {
+                    if (first_red) {
+                        d.rank = 0;
+                        d.kmat = B.kmat_off(t, 0);
+                        first_red = false;
+                    }
+                    return;
+                }
+                if (level < 1 || i > ft.m) return;
+                int site = t, fp = i - 1;
+                d.rank = (long long)B.ti.rank(1, &site, &fp);
+                d.kmat = B.kmat_off(t, ft.keep[i - 1]);
+            });
+            if (level >= 2 && rp.spawn_site >= 0) {
+                int s = rp.spawn_site;
+                B.dfs_group(1, {}, s, h.factors[s].m, B.group_bufs[1]);
+            }
+        }
+        if (N == 0) {
+            Launch l;
+            l.kind = L_REDUCE2;
+            l.src = B.phi[0];
+            l.dst = mainb;
+            l.grid = std::max(1, std::min<int>(E.sm_count * 4, (int)std::max<long long>(1, B.dim / (2 * kThreads * 16))));
+            B.partial_doubles = std::max(B.partial_doubles, (size_t)l.grid * 8);
+            B.L.push_back(l);
+            Launch f;
+            f.kind = L_FINISH;
+            f.n_red = 1;
+            f.fin_grid = l.grid;
+            f.desc_off = B.descs.size();
+            B.descs.push_back({0, 0, 0});
+            for (int i = 1; i < 4; ++i) B.descs.push_back({-1, 0, 0});
+            B.L.push_back(f);
+        }
+    }
+    {
+        Launch l;
+        l.kind = L_SUM;
+        B.L.push_back(l);
+    }
+
+    // --- aux allocation: ops, mats, ckpt table, kmats, descs, partials, term values, level offsets, result
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t off_ops = 0;
+    size_t off_mats = align(off_ops + B.dops.size() * sizeof(DevOp) + 1);
+    size_t off_ckpt = align(off_mats + B.tab.mats.size() * sizeof(float2) + 1);
+    size_t off_kmat = align(off_ckpt + n_phi * sizeof(float2*));
+    size_t off_desc = align(off_kmat + B.tab.kmats.size() * sizeof(double));
+    size_t off_part = align(off_desc + B.descs.size() * sizeof(FinishDesc) + 1);
+    size_t off_vals = align(off_part + std::max<size_t>(B.partial_doubles, 8) * sizeof(double));
+    size_t off_loff = align(off_vals + std::max<uint64_t>(B.ti.total, 1) * sizeof(double));
+    size_t off_res = align(off_loff + (level + 2) * sizeof(long long));
+    E.aux_bytes = align(off_res + sizeof(nqs_result));
+    E.aux = dev_alloc(E.aux_bytes, stream);
+    if (!E.aux) {
+        E.aux_bytes = 0;
+        engine_release(E, stream);
+        return NQS_ERR_NOMEM;
+    }
+    char* ab = (char*)E.aux;
+    DevOp* dops_dev = (DevOp*)(ab + off_ops);
+    B.ckpt_dev = (float2**)(ab + off_ckpt);
+    float2* mats_dev = (float2*)(ab + off_mats);
+    float2** ckpt_dev = (float2**)(ab + off_ckpt);
+    E.kmats_dev = (double*)(ab + off_kmat);
+    E.desc_dev = (FinishDesc*)(ab + off_desc);
+    E.partials = (double*)(ab + off_part);
+    E.term_vals = (double*)(ab + off_vals);
+    E.level_off_dev = (long long*)(ab + off_loff);
+    E.res_dev = (nqs_result*)(ab + off_res);
+
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<long long> loff(level + 2);
+    for (int u = 0; u <= level + 1; ++u) loff[u] = (long long)B.ti.level_offset[u];
+    int rc = NQS_OK;
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        if (bytes && rc == NQS_OK) rc = cuda_err(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+    };
+    up(dops_dev, B.dops.data(), B.dops.size() * sizeof(DevOp));
+    up(mats_dev, B.tab.mats.data(), B.tab.mats.size() * sizeof(float2));
+    up(ckpt_dev, B.phi.data(), n_phi * sizeof(float2*));
+    up(E.kmats_dev, B.tab.kmats.data(), B.tab.kmats.size() * sizeof(double));
+    up(E.desc_dev, B.descs.data(), B.descs.size() * sizeof(FinishDesc));
+    up(E.level_off_dev, loff.data(), loff.size() * sizeof(long long));
+    if (rc == NQS_OK) rc = cuda_err(cudaMemsetAsync(E.term_vals, 0, std::max<uint64_t>(B.ti.total, 1) * sizeof(double), st));
+    // the uploads read pageable host memory: make sure they completed before the builder goes away
+    if (rc == NQS_OK) rc = cuda_err(cudaStreamSynchronize(st));
+    if (rc != NQS_OK) {
+        engine_release(E, stream);
+        return rc;
+    }
+    // rebase pass arguments onto the device tables
+    for (auto& l : B.L) {
+        if (l.kind != L_PASS) continue;
+        l.args.ops = dops_dev + l.op_index;
+        l.args.mats = mats_dev;
+        l.args.ckpt = ckpt_dev;
+        l.args.partials = E.partials;
+    }
+    E.launches = std::move(B.L);
+    E.level = level;
+    E.psi_kind = psi->kind;
+    E.v_kind = v->kind;
+    E.psi_bits = psi->bits;
+    E.v_bits = v->bits;
+    E.psi_dev = psi->dev;
+    E.v_dev = v->dev;
+    E.n_terms = (long long)B.ti.total;
+    E.eff_level = level;
+    // truncation bound: sum_{|S|>l} prod ||M-bar|| prod ||M'||
+    std::vector<double> poly(1, 1.0);
+    for (int s = 0; s < N; ++s) {
+        std::vector<double> nx(poly.size() + 1, 0.0);
+        for (size_t i = 0; i < poly.size(); ++i) {
+            nx[i] += poly[i] * h.factors[s].norm_dom;
+            nx[i + 1] += poly[i] * h.factors[s].norm_rest;
+        }
+        poly.swap(nx);
+    }
+    double bnd = 0;
+    for (size_t i = level + 1; i < poly.size(); ++i) bnd += poly[i];
+    E.bound = bnd;
+    return NQS_OK;
+}
+
+static int launch_pass(const Launch& l, cudaStream_t st) {
+    if (l.S == 1) pass_kernel<1><<<l.grid, kThreads, l.smem, st>>>(l.args);
+    else if (l.S == 2) pass_kernel<2><<<l.grid, kThreads, l.smem, st>>>(l.args);
+    else pass_kernel<3><<<l.grid, kThreads, l.smem, st>>>(l.args);
+    return cuda_err(cudaGetLastError());
+}
+
+static int run_schedule(Handle& h, Engine& E, cudaStream_t st) {
+    const long long dim = 1ll << h.plan.n;
+    int rc = NQS_OK;
+    int fill_grid = (int)std::max<long long>(1, std::min<long long>(E.sm_count * 8, dim / 512));
+    for (const Launch& l : E.launches) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        int kind = (l.kind == L_PASS) ? 0 : (l.kind == L_FINISH || l.kind == L_SUM || l.kind == L_REDUCE2) ? 1 : 2;
+        if (h.profiling) {
+            if (E.ev_next >= E.ev_pool.size()) {
+                cudaEvent_t a, b;
+                cudaEventCreate(&a);
+                cudaEventCreate(&b);
+                E.ev_pool.push_back({a, b});
+            }
+            e0 = E.ev_pool[E.ev_next].first;
+            e1 = E.ev_pool[E.ev_next].second;
+            E.ev_used.push_back({kind, l.bytes});
+            ++E.ev_next;
+            cudaEventRecord(e0, st);
+        }
+        switch (l.kind) {
+            case L_PASS: rc = launch_pass(l, st); break;
+            case L_FINISH:
+                finish_kernel<<<l.n_red, kThreads, 0, st>>>(E.partials, l.fin_grid, E.desc_dev + l.desc_off, E.kmats_dev,
+                                                            E.term_vals);
+                rc = cuda_err(cudaGetLastError());
+                break;
+            case L_FILL:
+                basis_fill_kernel<<<fill_grid, kThreads, 0, st>>>(l.dst, dim, l.bits);
+                rc = cuda_err(cudaGetLastError());
+                break;
+            case L_COPY:
+                rc = cuda_err(cudaMemcpyAsync(l.dst, l.src, dim * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+                break;
+            case L_REDUCE2:
+                reduce2x2_kernel<<<l.grid, kThreads, 0, st>>>(l.src, l.dst, h.plan.n, 0, E.partials);
+                rc = cuda_err(cudaGetLastError());
+                break;
+            case L_SUM:
+                level_sum_kernel<<<1, kThreads, 0, st>>>(E.term_vals, E.level_off_dev, E.eff_level, E.res_dev, E.bound,
+                                                         E.n_terms);
+                rc = cuda_err(cudaGetLastError());
+                break;
+        }
+        if (h.profiling) cudaEventRecord(e1, st);
+        if (rc != NQS_OK) return rc;
+    }
+    return rc;
+}
+
+int engine_fidelity(Handle& h, const nqs_state* psi, const nqs_state* v, int level, nqs_result* out, void* stream) {
+    if (!h.eng) h.eng = new Engine();
+    Engine& E = *h.eng;
+    int rc = engine_init(E);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = build_schedule(h, E, psi, v, level, stream);
+    if (rc) return rc;
+    if (h.profiling) {
+        // fold finished timings of earlier calls before reusing the event pool
+        cudaStreamSynchronize(E.last_stream);
+        for (size_t i = 0; i < E.ev_used.size(); ++i) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, E.ev_pool[i].first, E.ev_pool[i].second);
+            nqs_kernel_stats& s = h.stats[E.ev_used[i].first];
+            s.launches += 1;
+            s.total_ms += ms;
+            s.algorithmic_bytes += E.ev_used[i].second;
+        }
+        E.ev_used.clear();
+        E.ev_next = 0;
+    }
+    rc = run_schedule(h, E, st);
+    if (rc) return rc;
+    E.last_stream = st;
+    E.has_result = true;
+    rc = cuda_err(cudaMemcpyAsync(out, E.res_dev, sizeof(nqs_result), cudaMemcpyDefault, st));
+    return rc;
+}
+
+int engine_collect_stats(Handle& h) {
+    if (!h.eng) return NQS_OK;
+    Engine& E = *h.eng;
+    if (cudaStreamSynchronize(E.last_stream) != cudaSuccess) return NQS_ERR_CUDA;
+    for (size_t i = 0; i < E.ev_used.size(); ++i) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, E.ev_pool[i].first, E.ev_pool[i].second);
+        nqs_kernel_stats& s = h.stats[E.ev_used[i].first];
+        s.launches += 1;
+        s.total_ms += ms;
+        s.algorithmic_bytes += E.ev_used[i].second;
+    }
+    E.ev_used.clear();
+    E.ev_next = 0;
+    return NQS_OK;
+}
+
+int engine_term_values(Handle& h, double* out, size_t cap, size_t* count) {
+    if (!h.eng || !h.eng->has_result) return NQS_ERR_ORDER;
+    Engine& E = *h.eng;
+    *count = (size_t)E.n_terms;
+    size_t nb = std::min<size_t>(cap, (size_t)E.n_terms) * sizeof(double);
+    if (cudaStreamSynchronize(E.last_stream) != cudaSuccess) return NQS_ERR_CUDA;
+    if (nb && cudaMemcpy(out, E.term_vals, nb, cudaMemcpyDeviceToHost) != cudaSuccess) return NQS_ERR_CUDA;
+    return NQS_OK;
+}
+
+void engine_destroy(Handle& h) {
+    if (!h.eng) return;
+    Engine& E = *h.eng;
+    if (E.last_stream) cudaStreamSynchronize(E.last_stream);
+    engine_release(E, E.last_stream);
+    for (auto& pr : E.ev_pool) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    delete h.eng;
+    h.eng = nullptr;
+}
+
+uint64_t engine_workspace_bytes(const Handle& h) {
+    return h.eng ? (uint64_t)(h.eng->buf_bytes + h.eng->aux_bytes) : 0;
+}
+
+// grid of the standalone reduction: about 16 pairs per thread per round,
+// capped at 4 blocks per SM and 2048 blocks
+static int reduced_matrix_grid(int n, int sms) {
+    long long npairs = 1ll << (n - 1);
+    long long g = (npairs + 16ll * kThreads - 1) / (16ll * kThreads);
+    return (int)std::max<long long>(1, std::min<long long>(std::min<long long>((long long)sms * 4, g), 2048));
+}
+
+static size_t reduced_matrix_scratch(int grid) { return ((size_t)grid * 8 + 8) * sizeof(double); }
+
+size_t engine_reduced_matrix_scratch_bytes(int n) {
+    // upper bound over SM counts: the grid never exceeds 2048 blocks
+    long long npairs = 1ll << (n - 1);
+    long long g = std::min<long long>(2048, std::max<long long>(1, (npairs + 16ll * kThreads - 1) / (16ll * kThreads)));
+    return reduced_matrix_scratch((int)g);
+}
+
+int engine_reduced_matrix(const void* phi, const void* chi, int n, int qubit, double* R_out, void* scratch,
+                          size_t scratch_bytes, void* stream) {
+    int dev;
+    if (cudaGetDevice(&dev) != cudaSuccess) return NQS_ERR_CUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return NQS_ERR_CUDA;
+    const int grid = reduced_matrix_grid(n, sms);
+    if (scratch_bytes < reduced_matrix_scratch(grid)) return NQS_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    double* part = (double*)scratch;
+    double* R = part + (size_t)grid * 8;
+    reduce2x2_kernel<<<grid, kThreads, 0, st>>>((const float2*)phi, (const float2*)chi, n, qubit, part);
+    if (cudaGetLastError() != cudaSuccess) return NQS_ERR_CUDA;
+    partials_sum_kernel<<<1, kThreads, 0, st>>>(part, grid, R);
+    if (cudaGetLastError() != cudaSuccess) return NQS_ERR_CUDA;
+    if (cudaMemcpyAsync(R_out, R, 8 * sizeof(double), cudaMemcpyDefault, st) != cudaSuccess) return NQS_ERR_CUDA;
+    return NQS_OK;
+}
+
+}  // namespace nqs

@@ -1,0 +1,239 @@
+// Sweep planner: one linear operation order shared by every sweep, then
+// segmentation of that order into tile passes.
+//
+// Every noise site becomes an OP_SITE carrying its dominant factor K_0
+// (Sec. IV: M' = U_0 (x) V_0); the non-dominant factors enter only through
+// the site's reductions and spawns.  Gates are fused while reading the
+// circuit: an operation is multiplied into the last operation touching its
+// qubits when that operation acts on a superset of them, is not a site, and
+// is not diagonal unless the new one is too (diagonal operations never need
+// their qubits inside the tile, so they are kept diagonal; CNOT-RZ-CNOT
+// collapses into one diagonal two-qubit phase).  Moving a gate past
+// operations on other qubits, including sites, is exact: the forward,
+// backward and branch sweeps all use this one order, so every checkpoint
+// <phi_s| and |chi_s> is cut at the same place.
+//
+// A pass keeps 2^k amplitudes in shared memory: the lowest c qubits (for
+// contiguous 256-byte runs in HBM) plus the qubits of the operations it
+// applies.  Diagonal operations on qubits outside the tile read the qubit's
+// value from the tile's base index.
+#include <algorithm>
+#include <cmath>
+
+#include "nqs_internal.h"
+
+namespace nqs {
+
+namespace {
+
+bool is_diag2(const std::array<cd, 16>& m) {
+    double mx = std::max(std::abs(m[0]), std::abs(m[3]));
+    double off = std::max(std::abs(m[1]), std::abs(m[2]));
+    return off <= 1e-14 * mx || (off == 0.0);
+}
+
+bool is_diag4(const std::array<cd, 16>& m) {
+    double mx = 0, off = 0;
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            double a = std::abs(m[4 * r + c]);
+            if (r == c) mx = std::max(mx, a);
+            else off = std::max(off, a);
+        }
+    return off <= 1e-14 * mx || off == 0.0;
+}
+
+// a 1q matrix on position `pos` (0 = first/more significant qubit) of a pair
+std::array<cd, 16> expand_1q(const std::array<cd, 16>& m2, int pos) {
+    std::array<cd, 16> out{};
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            int r0 = r >> 1, r1 = r & 1, c0 = c >> 1, c1 = c & 1;
+            if (pos == 0) out[4 * r + c] = (r1 == c1) ? m2[2 * r0 + c0] : cd(0);
+            else out[4 * r + c] = (r0 == c0) ? m2[2 * r1 + c1] : cd(0);
+        }
+    return out;
+}
+
+std::array<cd, 16> swap_pair(const std::array<cd, 16>& m) {
+    // reorder a 4x4 from (q0, q1) to (q1, q0) indexing
+    auto sw = [](int i) { return ((i & 1) << 1) | (i >> 1); };
+    std::array<cd, 16> out{};
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) out[4 * sw(r) + sw(c)] = m[4 * r + c];
+    return out;
+}
+
+std::array<cd, 16> matmul(const std::array<cd, 16>& a, const std::array<cd, 16>& b, int d) {
+    std::array<cd, 16> out{};
+    for (int r = 0; r < d; ++r)
+        for (int c = 0; c < d; ++c) {
+            cd s = 0;
+            for (int k = 0; k < d; ++k) s += a[d * r + k] * b[d * k + c];
+            out[d * r + c] = s;
+        }
+    return out;
+}
+
+bool op_is_diag(const HostOp& o) { return o.type == OP_D1 || o.type == OP_D2; }
+
+}  // namespace
+
+void build_plan(const Circuit& c, const std::vector<Factors>& f, int tile_qubits, Plan& p) {
+    p = Plan{};
+    p.n = c.n;
+    p.k = std::min(c.n, tile_qubits);
+    p.c = std::min(c.n, 5);
+    std::vector<int> last(c.n, -1);
+
+    auto append = [&](HostOp op) {
+        int qa = op.q0, qb = op.q1;
+        if (op.type != OP_SITE) {
+            int cand = last[qa];
+            bool ok = cand >= 0 && (qb < 0 || last[qb] == cand);
+            if (ok) {
+                HostOp& t = p.ops[cand];
+                bool t_two = (t.type == OP_G2 || t.type == OP_D2);
+                bool t_one = (t.type == OP_G1 || t.type == OP_D1);
+                bool covers = (qb < 0) ? ((t_one && t.q0 == qa) || (t_two && (t.q0 == qa || t.q1 == qa)))
+                                       : (t_two && ((t.q0 == qa && t.q1 == qb) || (t.q0 == qb && t.q1 == qa)));
+                bool diag_ok = !op_is_diag(t) || op_is_diag(op);
+                if (t.type != OP_SITE && covers && diag_ok) {
+                    bool new_two = (op.type == OP_G2 || op.type == OP_D2);
+                    if (t_one) {
+                        t.m = matmul(op.m, t.m, 2);
+                    } else {
+                        std::array<cd, 16> m4;
+                        if (!new_two) m4 = expand_1q(op.m, qa == t.q0 ? 0 : 1);
+                        else m4 = (op.q0 == t.q0) ? op.m : swap_pair(op.m);
+                        t.m = matmul(m4, t.m, 4);
+                    }
+                    bool d = t_one ? is_diag2(t.m) : is_diag4(t.m);
+                    if (t_one) t.type = d ? OP_D1 : OP_G1;
+                    else t.type = d ? OP_D2 : OP_G2;
+                    return;
+                }
+            }
+        }
+        p.ops.push_back(op);
+        int idx = (int)p.ops.size() - 1;
+        last[qa] = idx;
+        if (qb >= 0) last[qb] = idx;
+    };
+
+    auto gate_op = [&](const Gate& g) {
+        HostOp o;
+        o.q0 = g.q0;
+        if (gate_is_two_qubit(g.kind)) {
+            o.q1 = g.q1;
+            Mat4 m = gate_matrix_2q(g);
+            std::copy(m.begin(), m.end(), o.m.begin());
+            o.type = is_diag4(o.m) ? OP_D2 : OP_G2;
+        } else {
+            Mat2 m = gate_matrix_1q(g);
+            for (int e = 0; e < 4; ++e) o.m[e] = m[e];
+            o.type = is_diag2(o.m) ? OP_D1 : OP_G1;
+        }
+        return o;
+    };
+    auto site_op = [&](int s) {
+        HostOp o;
+        o.type = OP_SITE;
+        o.q0 = c.noises[s].qubit;
+        o.site = s;
+        for (int e = 0; e < 4; ++e) o.m[e] = f[s].K[0][e];
+        o.diag = is_diag2(o.m);
+        if (o.diag) o.m[1] = o.m[2] = cd(0);
+        return o;
+    };
+
+    p.site_pos.assign(c.noises.size(), -1);
+    size_t ns = 0;
+    auto flush_sites = [&](int g) {
+        while (ns < c.noises.size() && c.noises[ns].after_gate == g) {
+            append(site_op((int)ns));
+            p.site_pos[ns] = (int)p.ops.size() - 1;
+            ++ns;
+        }
+    };
+    flush_sites(-1);
+    for (size_t g = 0; g < c.gates.size(); ++g) {
+        append(gate_op(c.gates[g]));
+        flush_sites((int)g);
+    }
+    // exact zeros for the off-diagonals of diagonal operations
+    for (auto& o : p.ops) {
+        if (o.type == OP_D1) o.m[1] = o.m[2] = cd(0);
+        if (o.type == OP_D2)
+            for (int r = 0; r < 4; ++r)
+                for (int cc = 0; cc < 4; ++cc)
+                    if (r != cc) o.m[4 * r + cc] = cd(0);
+    }
+    p.free_passes = segment(p, false, 8);
+    p.sitecut_passes = segment(p, true, 8);
+}
+
+std::vector<PassSpec> segment(const Plan& p, bool cut_after_sites, int max_sites_per_pass) {
+    std::vector<PassSpec> out;
+    const int nops = (int)p.ops.size();
+    auto needs = [&](const HostOp& o, int q[2]) {
+        int cnt = 0;
+        if (o.type == OP_G1 || o.type == OP_SITE) q[cnt++] = o.q0;
+        if (o.type == OP_G2) {
+            q[cnt++] = o.q0;
+            q[cnt++] = o.q1;
+        }
+        return cnt;
+    };
+    int i = 0;
+    if (nops == 0) {
+        PassSpec ps;
+        for (int q = 0; q < p.k; ++q) ps.local.push_back(q);
+        ps.op_begin = ps.op_end = 0;
+        out.push_back(ps);
+        return out;
+    }
+    while (i < nops) {
+        std::vector<char> in(p.n, 0);
+        int count = 0;
+        for (int q = 0; q < p.c; ++q) {
+            in[q] = 1;
+            ++count;
+        }
+        PassSpec ps;
+        ps.op_begin = i;
+        int sites = 0;
+        while (i < nops) {
+            int q[2];
+            int cnt = needs(p.ops[i], q);
+            int extra = 0;
+            for (int j = 0; j < cnt; ++j) extra += in[q[j]] ? 0 : 1;
+            if (cnt == 2 && q[0] == q[1]) extra = in[q[0]] ? 0 : 1;
+            if (count + extra > p.k) break;
+            for (int j = 0; j < cnt; ++j)
+                if (!in[q[j]]) {
+                    in[q[j]] = 1;
+                    ++count;
+                }
+            bool site = p.ops[i].type == OP_SITE;
+            ++i;
+            if (site) {
+                ++sites;
+                if (cut_after_sites || sites >= max_sites_per_pass) break;
+            }
+        }
+        ps.op_end = i;
+        // pad the tile to exactly k qubits with the lowest unused ones
+        for (int q = 0; q < p.n && count < p.k; ++q)
+            if (!in[q]) {
+                in[q] = 1;
+                ++count;
+            }
+        for (int q = 0; q < p.n; ++q)
+            if (in[q]) ps.local.push_back(q);
+        out.push_back(ps);
+    }
+    return out;
+}
+
+}  // namespace nqs

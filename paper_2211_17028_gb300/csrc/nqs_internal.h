@@ -1,0 +1,128 @@
+// Internal types of libnqs shared by the host planner (C++) and the sweep
+// engine (CUDA).  Nothing here is part of the C ABI.
+#pragma once
+
+#include <array>
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/nqs.h"
+
+namespace nqs {
+
+using cd = std::complex<double>;
+using Mat2 = std::array<cd, 4>;    // row-major 2x2
+using Mat4 = std::array<cd, 16>;   // row-major 4x4, index 2*b(q0)+b(q1)
+
+// ---------------------------------------------------------------- circuit IR
+enum GateKind : int { G_H, G_X, G_Y, G_Z, G_T, G_RX, G_RY, G_RZ, G_U3, G_CZ, G_CX };
+
+struct Gate {
+    GateKind kind;
+    int q0 = -1, q1 = -1;
+    double p[3] = {0, 0, 0};
+};
+
+struct NoiseSite {
+    int after_gate = -1;               // -1: before gate 0
+    int qubit = 0;
+    std::vector<Mat2> kraus;
+};
+
+struct Circuit {
+    int n = 0;
+    std::vector<Gate> gates;
+    std::vector<NoiseSite> noises;     // ordered by after_gate (stable)
+};
+
+// Parse the text format; returns NQS_OK or NQS_ERR_PARSE / NQS_ERR_UNSUPPORTED.
+int parse_circuit(const char* text, Circuit& out, std::string& err);
+bool gate_is_two_qubit(GateKind k);
+Mat2 gate_matrix_1q(const Gate& g);
+Mat4 gate_matrix_2q(const Gate& g);
+
+// ------------------------------------------------------------ noise factors
+struct Factors {
+    double d[4];            // singular values of M~, descending
+    Mat2 K[4];              // K_i = sqrt(d_i) A_i, A_i = reshape of the i-th singular vector
+    int m = 3;              // number of non-dominant factors kept in the expansion
+    int keep[3] = {1, 2, 3};// their factor indices
+    double norm_dom;        // ||U_0 (x) V_0||_2 = d_0 * ... (spectral norm of M')
+    double norm_rest;       // ||sum_{i>=1} U_i (x) V_i||_2
+};
+
+// Returns NQS_OK, NQS_ERR_NOT_CPTP or NQS_ERR_NOT_DOMINANT.
+int factor_noise(const NoiseSite& s, bool prune_zero_rank, Factors& out);
+// Hermitian 4x4 eigen-decomposition by cyclic complex Jacobi rotations.
+void hermitian_jacobi4(const Mat4& a, double evals[4], Mat4& evecs_columns);
+
+// --------------------------------------------------------------- enumeration
+struct TermIndex {
+    int N = 0;
+    int level = 0;
+    std::vector<int> m;                          // kept factors per site
+    std::vector<std::vector<uint64_t>> E;        // E[j][a] = e_j(m_a .. m_{N-1})
+    std::vector<uint64_t> level_offset;          // first rank of each level
+    uint64_t total = 0;
+    void build(const std::vector<int>& m_per_site, int level);
+    // rank of a kept term; sites ascending, factor positions 0..m_s-1
+    uint64_t rank(int k, const int* sites, const int* fpos) const;
+};
+
+// --------------------------------------------------------------------- plan
+enum OpType : int { OP_G1 = 1, OP_G2 = 2, OP_D1 = 3, OP_D2 = 4, OP_SITE = 5 };
+
+struct HostOp {
+    OpType type;
+    int q0 = -1, q1 = -1;
+    int site = -1;                 // OP_SITE
+    std::array<cd, 16> m{};        // G1/D1: 4 (D1 uses m[0], m[3]); G2/D2: 16; SITE: K_0
+    bool diag = false;             // SITE: K_0 is diagonal
+};
+
+struct PassSpec {
+    std::vector<int> local;        // tile qubits, ascending (low `c` qubits always included)
+    int op_begin = 0, op_end = 0;  // range in the linear op list
+};
+
+struct Plan {
+    int n = 0, k = 0, c = 0;       // qubits, tile qubits, always-local low qubits
+    std::vector<HostOp> ops;       // linear op order used by every sweep
+    std::vector<int> site_pos;     // op index of each site's OP_SITE
+    std::vector<PassSpec> free_passes;     // cuts only where locality forces them
+    std::vector<PassSpec> sitecut_passes;  // additionally cut after every OP_SITE
+};
+
+void build_plan(const Circuit& c, const std::vector<Factors>& f, int tile_qubits, Plan& out);
+std::vector<PassSpec> segment(const Plan& p, bool cut_after_sites, int max_sites_per_pass);
+
+// ------------------------------------------------------------------- handle
+struct Engine;   // device-side state (engine.cu)
+
+struct Handle {
+    Circuit circ;
+    bool prepared = false;
+    std::vector<Factors> factors;
+    Plan plan;
+    Engine* eng = nullptr;
+    bool profiling = false;
+    nqs_kernel_stats stats[3] = {};
+};
+
+// engine entry points (engine.cu)
+int engine_fidelity(Handle& h, const nqs_state* psi, const nqs_state* v, int level,
+                    nqs_result* out, void* stream);
+int engine_term_values(Handle& h, double* out, size_t cap, size_t* count);
+void engine_destroy(Handle& h);
+uint64_t engine_workspace_bytes(const Handle& h);
+int engine_reduced_matrix(const void* phi, const void* chi, int n, int qubit, double* R_out,
+                          void* scratch, size_t scratch_bytes, void* stream);
+size_t engine_reduced_matrix_scratch_bytes(int n);
+
+// allocator (capi.cpp)
+void* dev_alloc(size_t bytes, void* stream);
+void dev_free(void* p, size_t bytes, void* stream);
+
+}  // namespace nqs

@@ -1,0 +1,357 @@
+"""Python binding of libnqs (include/nqs.h): argument marshalling only.
+
+Every function keeps the C name and forwards to the shared library; all
+computation happens in the library's CUDA kernels.  PyTorch provides device
+memory (the library's allocator hook is pointed at torch's caching
+allocator) and streams.  Importing this module fails loudly when the
+compiled library is missing: there is no fallback.
+"""
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnqs.so")
+
+NQS_OK = 0
+NQS_ERR_ARG = 1
+NQS_ERR_PARSE = 2
+NQS_ERR_NOT_CPTP = 3
+NQS_ERR_NOT_DOMINANT = 4
+NQS_ERR_NOMEM = 5
+NQS_ERR_CUDA = 6
+NQS_ERR_ORDER = 7
+NQS_ERR_DEVICE_TIMEOUT = 8
+NQS_ERR_UNSUPPORTED = 9
+
+NQS_STATE_BASIS = 0
+NQS_STATE_DENSE = 1
+NQS_STATE_IDEAL = 2
+NQS_PREP_PRUNE_ZERO_RANK = 1
+NQS_MAX_LEVEL = 16
+
+
+class NqsError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s: %s (code %d)" % (where, _lib().nqs_strerror(code).decode(), code))
+
+
+class nqs_state(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("bits", ctypes.c_uint64), ("dev", ctypes.c_void_p)]
+
+
+class nqs_noise(ctypes.Structure):
+    _fields_ = [("after_gate", ctypes.c_int32), ("qubit", ctypes.c_uint32), ("n_kraus", ctypes.c_uint32),
+                ("kraus", ctypes.POINTER(ctypes.c_double))]
+
+
+class nqs_result(ctypes.Structure):
+    _fields_ = [("F", ctypes.c_double), ("T", ctypes.c_double * (NQS_MAX_LEVEL + 1)),
+                ("imag_residual", ctypes.c_double), ("n_terms", ctypes.c_uint64), ("bound", ctypes.c_double),
+                ("level", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+    def to_dict(self):
+        return {"F": self.F, "T": [self.T[u] for u in range(self.level + 1)],
+                "imag_residual": self.imag_residual, "n_terms": int(self.n_terms), "bound": self.bound,
+                "level": self.level, "status": self.status}
+
+
+class nqs_info(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("n_gates", ctypes.c_int32), ("n_sites", ctypes.c_int32),
+                ("n_ops", ctypes.c_int32), ("n_passes", ctypes.c_int32), ("tile_qubits", ctypes.c_int32),
+                ("workspace_bytes", ctypes.c_uint64)]
+
+
+class nqs_kernel_stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
+                ("algorithmic_bytes", ctypes.c_double)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_L = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "nqs_set_allocator": (ctypes.c_int, [ALLOC_FN, FREE_FN, ctypes.c_void_p]),
+    "nqs_load_circuit": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "nqs_prepare_noise": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(nqs_noise), ctypes.c_size_t,
+                                         ctypes.c_uint32]),
+    "nqs_fidelity": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(nqs_state), ctypes.POINTER(nqs_state),
+                                    ctypes.c_int, ctypes.POINTER(nqs_result), ctypes.c_void_p]),
+    "nqs_batch_fidelity": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t,
+                                          ctypes.POINTER(nqs_state), ctypes.POINTER(nqs_state),
+                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(nqs_result),
+                                          ctypes.c_void_p]),
+    "nqs_enumerate_terms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
+                                           ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "nqs_noise_factors": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double)]),
+    "nqs_term_values": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t,
+                                       ctypes.POINTER(ctypes.c_size_t)]),
+    "nqs_truncation_bound": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "nqs_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(nqs_info)]),
+    "nqs_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "nqs_get_kernel_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(nqs_kernel_stats)]),
+    "nqs_reduced_matrix": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "nqs_reduced_matrix_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int]),
+    "nqs_destroy": (None, [ctypes.c_void_p]),
+    "nqs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "nqs_version": (ctypes.c_char_p, []),
+}
+
+
+def _lib():
+    global _L
+    if _L is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libnqs.so is not built (run __graft_entry__.build()): " + LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _L = L
+    return _L
+
+
+def library():
+    return _lib()
+
+
+def _check(rc, where):
+    if rc != NQS_OK:
+        raise NqsError(rc, where)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# --------------------------------------------------------------- allocator
+_alloc_refs = None
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through torch's caching allocator."""
+    global _alloc_refs
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+    _check(_lib().nqs_set_allocator(a, f, None), "nqs_set_allocator")
+    _alloc_refs = (a, f)
+
+
+def use_cuda_allocator():
+    global _alloc_refs
+    _check(_lib().nqs_set_allocator(ALLOC_FN(), FREE_FN(), None), "nqs_set_allocator")
+    _alloc_refs = None
+
+
+def nqs_set_allocator(alloc, release, ctx=None):
+    _check(_lib().nqs_set_allocator(alloc, release, ctx), "nqs_set_allocator")
+
+
+# --------------------------------------------------------------- states
+def basis(bits):
+    return nqs_state(NQS_STATE_BASIS, int(bits), None)
+
+
+def dense(tensor):
+    """A complex64 CUDA tensor (or its data pointer)."""
+    ptr = tensor if isinstance(tensor, int) else tensor.data_ptr()
+    return nqs_state(NQS_STATE_DENSE, 0, ctypes.c_void_p(ptr))
+
+
+def ideal():
+    return nqs_state(NQS_STATE_IDEAL, 0, None)
+
+
+def _as_state(s):
+    if isinstance(s, nqs_state):
+        return s
+    if isinstance(s, dict):
+        if s["kind"] == "basis":
+            return basis(s["bits"])
+        if s["kind"] == "ideal":
+            return ideal()
+        if s["kind"] == "dense":
+            return dense(s["tensor"])
+    raise TypeError("unsupported state descriptor")
+
+
+# --------------------------------------------------------------- entry points
+def nqs_load_circuit(ir_text):
+    h = ctypes.c_void_p()
+    _check(_lib().nqs_load_circuit(ir_text.encode() if isinstance(ir_text, str) else ir_text, ctypes.byref(h)),
+           "nqs_load_circuit")
+    return h
+
+
+def _noise_array(sites):
+    import numpy as np
+    arr = (nqs_noise * len(sites))()
+    keep = []
+    for i, (after_gate, qubit, kraus) in enumerate(sites):
+        buf = np.ascontiguousarray(np.array([np.asarray(k, dtype=np.complex128).reshape(4) for k in kraus])
+                                   .view(np.float64).reshape(-1))
+        keep.append(buf)
+        arr[i] = nqs_noise(int(after_gate), int(qubit), len(kraus),
+                           buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return arr, keep
+
+
+def nqs_prepare_noise(h, sites=None, flags=0):
+    """sites: None (use the circuit text's noise records) or a list of
+    (after_gate, qubit, [2x2 Kraus matrices])."""
+    if sites is None:
+        _check(_lib().nqs_prepare_noise(h, None, 0, flags), "nqs_prepare_noise")
+    else:
+        arr, keep = _noise_array(sites)
+        _check(_lib().nqs_prepare_noise(h, arr, len(sites), flags), "nqs_prepare_noise")
+
+
+def nqs_fidelity(h, psi, v, level, stream=None, out=None):
+    """Returns the nqs_result (host copy; the call synchronises through the
+    pageable result copy unless `out` is a device/pinned nqs_result)."""
+    res = out if out is not None else nqs_result()
+    ps, vs = _as_state(psi), _as_state(v)
+    _check(_lib().nqs_fidelity(h, ctypes.byref(ps), ctypes.byref(vs), int(level), ctypes.byref(res),
+                               _stream_ptr(stream)), "nqs_fidelity")
+    return res
+
+
+def nqs_batch_fidelity(hs, psis, vs, levels, stream=None):
+    n = len(hs)
+    harr = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in hs])
+    parr = (nqs_state * n)(*[_as_state(p) for p in psis])
+    varr = (nqs_state * n)(*[_as_state(v) for v in vs])
+    larr = (ctypes.c_int * n)(*[int(x) for x in levels])
+    outs = (nqs_result * n)()
+    _check(_lib().nqs_batch_fidelity(harr, n, parr, varr, larr, outs, _stream_ptr(stream)),
+           "nqs_batch_fidelity")
+    return list(outs)
+
+
+def nqs_enumerate_terms(h, level):
+    cnt = ctypes.c_size_t()
+    _check(_lib().nqs_enumerate_terms(h, level, None, 0, ctypes.byref(cnt)), "nqs_enumerate_terms")
+    buf = (ctypes.c_uint64 * max(1, cnt.value))()
+    _check(_lib().nqs_enumerate_terms(h, level, buf, cnt.value, ctypes.byref(cnt)), "nqs_enumerate_terms")
+    return [int(buf[i]) for i in range(cnt.value)]
+
+
+def nqs_noise_factors(h, site):
+    import numpy as np
+    d = (ctypes.c_double * 4)()
+    k = (ctypes.c_double * 32)()
+    _check(_lib().nqs_noise_factors(h, site, d, k), "nqs_noise_factors")
+    kk = np.array(list(k)).view(np.complex128).reshape(4, 2, 2)
+    return np.array(list(d)), kk
+
+
+def nqs_term_values(h):
+    import numpy as np
+    cnt = ctypes.c_size_t()
+    _check(_lib().nqs_term_values(h, None, 0, ctypes.byref(cnt)), "nqs_term_values")
+    out = np.zeros(max(1, cnt.value), dtype=np.float64)
+    _check(_lib().nqs_term_values(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cnt.value,
+                                  ctypes.byref(cnt)), "nqs_term_values")
+    return out[:cnt.value]
+
+
+def nqs_truncation_bound(h, level):
+    out = ctypes.c_double()
+    _check(_lib().nqs_truncation_bound(h, level, ctypes.byref(out)), "nqs_truncation_bound")
+    return out.value
+
+
+def nqs_get_info(h):
+    info = nqs_info()
+    _check(_lib().nqs_get_info(h, ctypes.byref(info)), "nqs_get_info")
+    return {f: getattr(info, f) for f, _ in nqs_info._fields_}
+
+
+def nqs_set_profiling(h, on):
+    _check(_lib().nqs_set_profiling(h, int(bool(on))), "nqs_set_profiling")
+
+
+def nqs_get_kernel_stats(h, kind):
+    s = nqs_kernel_stats()
+    _check(_lib().nqs_get_kernel_stats(h, kind, ctypes.byref(s)), "nqs_get_kernel_stats")
+    return {"launches": int(s.launches), "total_ms": s.total_ms, "algorithmic_bytes": s.algorithmic_bytes}
+
+
+def nqs_reduced_matrix(phi, chi, n, qubit, r_out, scratch, scratch_bytes, stream=None):
+    """phi, chi, r_out, scratch: device pointers (ints) or tensors."""
+    def ptr(x):
+        return x if isinstance(x, int) else x.data_ptr()
+    _check(_lib().nqs_reduced_matrix(ctypes.c_void_p(ptr(phi)), ctypes.c_void_p(ptr(chi)), n, qubit,
+                                     ctypes.c_void_p(ptr(r_out)), ctypes.c_void_p(ptr(scratch)),
+                                     scratch_bytes, _stream_ptr(stream)), "nqs_reduced_matrix")
+
+
+def nqs_reduced_matrix_scratch_bytes(n):
+    return int(_lib().nqs_reduced_matrix_scratch_bytes(n))
+
+
+def nqs_destroy(h):
+    _lib().nqs_destroy(h)
+
+
+def nqs_strerror(code):
+    return _lib().nqs_strerror(code).decode()
+
+
+def nqs_version():
+    return _lib().nqs_version().decode()
+
+
+class NoisyCircuit:
+    """Owns one handle: circuit text in, noise prepared, fidelity calls."""
+
+    def __init__(self, ir_text, sites=None, flags=0):
+        self.h = nqs_load_circuit(ir_text)
+        try:
+            nqs_prepare_noise(self.h, sites, flags)
+        except Exception:
+            nqs_destroy(self.h)
+            raise
+
+    def fidelity(self, psi, v, level, stream=None):
+        return nqs_fidelity(self.h, psi, v, level, stream).to_dict()
+
+    def term_values(self):
+        return nqs_term_values(self.h)
+
+    def info(self):
+        return nqs_get_info(self.h)
+
+    def close(self):
+        if self.h is not None:
+            nqs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,179 @@
+"""Host side of the C ABI (no GPU): library exports, circuit reader, noise
+factors, canonical enumeration, bounds -- compared with the oracle."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from workloads import channels as ch
+from oracle import bounds as OB
+from oracle import expansion as OEX
+from oracle import ir as OIR
+from paper_2211_17028_gb300 import nqs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "nqs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nqs_[a-z0-9_]+)\s*\(", text)) - {"nqs_alloc_fn", "nqs_free_fn"})
+
+
+def test_library_exports_every_declared_symbol():
+    lib = nqs.library()
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert "sm_103a" in nqs.nqs_version()
+
+
+def test_binding_covers_every_declared_function():
+    for name in declared_functions():
+        assert hasattr(nqs, name), name
+
+
+def _handle(w, flags=0):
+    h = nqs.nqs_load_circuit(W.to_ir_text(w))
+    nqs.nqs_prepare_noise(h, None, flags)
+    return h
+
+
+def test_parse_errors_and_call_order():
+    with pytest.raises(nqs.NqsError) as e:
+        nqs.nqs_load_circuit("qubits 2\ngate h 0\n")
+    assert e.value.code == nqs.NQS_ERR_PARSE
+    for bad in ["nqs-ir 1\nqubits 2\ngate h 2\n", "nqs-ir 1\nqubits 2\ngate cz 0 0\n",
+                "nqs-ir 1\nqubits 2\ngate rx 0\n", "nqs-ir 1\nqubits 2\ngate foo 0\n",
+                "nqs-ir 1\nqubits 2\ngate h 0\nnoise 3 0 1 1 0 0 0 0 0 1 0\n",
+                "nqs-ir 1\nqubits 2\ngate h 0\ngate h 1\nnoise 1 0 1 1 0 0 0 0 0 1 0\nnoise 0 0 1 1 0 0 0 0 0 1 0\n"]:
+        with pytest.raises(nqs.NqsError) as e:
+            nqs.nqs_load_circuit(bad)
+        assert e.value.code == nqs.NQS_ERR_PARSE, bad
+    with pytest.raises(nqs.NqsError) as e:
+        nqs.nqs_load_circuit("nqs-ir 1\nqubits 40\n")
+    assert e.value.code == nqs.NQS_ERR_UNSUPPORTED
+    h = nqs.nqs_load_circuit("nqs-ir 1\nqubits 2\ngate h 0\n")
+    with pytest.raises(nqs.NqsError) as e:
+        nqs.nqs_enumerate_terms(h, 1)
+    assert e.value.code == nqs.NQS_ERR_ORDER
+    nqs.nqs_destroy(h)
+
+
+def test_noise_validation_errors():
+    h = nqs.nqs_load_circuit("nqs-ir 1\nqubits 2\ngate h 0\ngate cx 0 1\n")
+    bad = [np.eye(2) * 0.9]
+    with pytest.raises(nqs.NqsError) as e:
+        nqs.nqs_prepare_noise(h, [(0, 0, bad)])
+    assert e.value.code == nqs.NQS_ERR_NOT_CPTP
+    with pytest.raises(nqs.NqsError) as e:
+        nqs.nqs_prepare_noise(h, [(0, 1, ch.depolarizing_paper(0.75))])
+    assert e.value.code == nqs.NQS_ERR_NOT_DOMINANT
+    with pytest.raises(nqs.NqsError) as e:
+        nqs.nqs_prepare_noise(h, [(0, 2, ch.depolarizing_paper(0.1))])
+    assert e.value.code == nqs.NQS_ERR_ARG
+    with pytest.raises(nqs.NqsError) as e:
+        nqs.nqs_prepare_noise(h, [(1, 0, ch.depolarizing_paper(0.1)), (0, 0, ch.depolarizing_paper(0.1))])
+    assert e.value.code == nqs.NQS_ERR_ARG
+    nqs.nqs_prepare_noise(h, [(-1, 0, ch.amplitude_damping(0.1)), (1, 1, ch.phase_damping(0.2))])
+    assert nqs.nqs_get_info(h)["n_sites"] == 2
+    nqs.nqs_destroy(h)
+
+
+@pytest.mark.parametrize("seed,n,gates,noise", [(1, 3, 20, 4), (2, 5, 30, 6), (3, 4, 10, 9), (4, 6, 40, 0)])
+def test_enumeration_is_bit_identical_to_oracle(seed, n, gates, noise):
+    w = W.random_circuit(seed, n, gates, noise)
+    h = _handle(w)
+    N = w.n_noise
+    for level in range(0, 5):
+        assert nqs.nqs_enumerate_terms(h, level) == OEX.enumerate_records(N, level)
+    nqs.nqs_destroy(h)
+
+
+def test_enumeration_of_configurations():
+    for w, levels in ((W.c1_line6(), (1, 4)), (W.c2_grid20(), (1, 2)), (W.c3_qaoa30(), (2,))):
+        h = _handle(w)
+        for level in levels:
+            recs = nqs.nqs_enumerate_terms(h, level)
+            assert recs == OEX.enumerate_records(w.n_noise, level)
+            assert len(recs) == OEX.term_count(w.n_noise, level)
+        nqs.nqs_destroy(h)
+
+
+CHANNELS = [ch.depolarizing_paper(0.01), ch.amplitude_damping(0.03), ch.phase_damping(0.02),
+            ch.ad_pd(1e-3, 1e-3), ch.near_identity_channel(W.SplitMix64(5), 0.02, 3),
+            ch.near_identity_channel(W.SplitMix64(6), 0.05, 1), [np.eye(2, dtype=np.complex128)]]
+
+
+@pytest.mark.parametrize("idx", range(len(CHANNELS)))
+def test_noise_factors_match_oracle_svd(idx):
+    kraus = CHANNELS[idx]
+    h = nqs.nqs_load_circuit("nqs-ir 1\nqubits 1\ngate h 0\n")
+    nqs.nqs_prepare_noise(h, [(0, 0, kraus)])
+    d, K = nqs.nqs_noise_factors(h, 0)
+    do, u, v, _, _ = OEX.svd_factors(kraus)
+    assert np.allclose(d, do, atol=1e-14)
+    # the factors rebuild the channel: sum_i K_i (x) conj(K_i) = M
+    m = OEX.matrix_representation(kraus)
+    assert np.allclose(sum(np.kron(K[i], K[i].conj()) for i in range(4)), m, atol=1e-14)
+    # per eigenspace the products agree with the oracle's U_i (x) V_i (phase free)
+    groups = []
+    for i in range(4):
+        if groups and abs(d[i] - d[groups[-1][0]]) <= 1e-12 * max(d[0], 1e-300):
+            groups[-1].append(i)
+        else:
+            groups.append([i])
+    for g in groups:
+        mine = sum(np.kron(K[i], K[i].conj()) for i in g)
+        theirs = sum(np.kron(u[i], v[i]) for i in g)
+        assert np.allclose(mine, theirs, atol=1e-13)
+    nqs.nqs_destroy(h)
+
+
+def test_truncation_bound_matches_oracle():
+    w = W.random_circuit(8, 4, 25, 7, rate_lo=1e-3, rate_hi=3e-2)
+    h = _handle(w)
+    c = OIR.parse(W.to_ir_text(w))
+    kl = [z[2] for z in c.noises]
+    for level in range(0, 8):
+        assert nqs.nqs_truncation_bound(h, level) == pytest.approx(OB.per_site_bound(kl, level), rel=1e-12,
+                                                                   abs=1e-300)
+    nqs.nqs_destroy(h)
+
+
+def test_plan_shapes():
+    h = _handle(W.c3_qaoa30())
+    info = nqs.nqs_get_info(h)
+    assert info["n_qubits"] == 30 and info["n_sites"] == 20 and info["tile_qubits"] == 12
+    # CNOT-RZ-CNOT collapses into one diagonal phase: far fewer fused ops than gates
+    assert info["n_ops"] <= 30 + 4 * (45 + 30) + 20
+    assert info["n_passes"] >= 3
+    nqs.nqs_destroy(h)
+    h = _handle(W.c1_line6())
+    info = nqs.nqs_get_info(h)
+    assert info["n_passes"] == 1 and info["tile_qubits"] == 6
+    nqs.nqs_destroy(h)
+
+
+def test_prune_flag_drops_zero_rank_factors():
+    # amplitude damping has Kraus rank 2: with pruning only factor 1 remains
+    h = nqs.nqs_load_circuit("nqs-ir 1\nqubits 2\ngate h 0\ngate cx 0 1\n")
+    sites = [(0, 0, ch.amplitude_damping(0.05)), (1, 1, ch.amplitude_damping(0.02)),
+             (1, 0, ch.depolarizing_paper(0.01))]
+    nqs.nqs_prepare_noise(h, sites, nqs.NQS_PREP_PRUNE_ZERO_RANK)
+    recs = nqs.nqs_enumerate_terms(h, 2)
+    # per site kept factors: 1, 1, 3 -> level<=2 count = 1 + (1+1+3) + (1*1 + 1*3 + 1*3)
+    assert len(recs) == 1 + 5 + 7
+    for r in recs:
+        k = r & 15
+        for j in range(k):
+            f = (r >> (4 + 14 * j)) & 0x3FFF
+            site, fac = f & 0xFFF, f >> 12
+            if site < 2:
+                assert fac == 1
+    nqs.nqs_destroy(h)
