@@ -170,6 +170,8 @@ typedef struct {
     int32_t n_passes;           /* tile passes of one full sweep */
     int32_t tile_qubits;        /* qubits held in shared memory per tile */
     uint64_t workspace_bytes;   /* device bytes held by the handle */
+    uint64_t upload_bytes;      /* host-to-device bytes of the last schedule build */
+    uint64_t launches_per_call; /* kernels launched by one nqs_fidelity call */
 } nqs_info;
 
 int nqs_get_info(nqs_handle h, nqs_info* out);

@@ -247,6 +247,8 @@ int nqs_get_info(nqs_handle hh, nqs_info* out) {
         out->tile_qubits = h->plan.k;
     }
     out->workspace_bytes = engine_workspace_bytes(*h);
+    out->upload_bytes = engine_upload_bytes(*h);
+    out->launches_per_call = engine_launches_per_call(*h);
     return NQS_OK;
 }
 

@@ -31,433 +31,9 @@
 #include <vector>
 
 #include "nqs_internal.h"
+#include "sweep_types.h"
 
 namespace nqs {
-
-constexpr int kMaxTileQ = 12;          // 4096 amplitudes = 32 KB per state tile
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-constexpr int kMaxEvents = 8;          // reductions per pass (planner cuts passes accordingly)
-constexpr int kMaxQ = 34;
-
-enum : int {
-    FL_REDUCE = 1,
-    FL_SPAWN = 2,
-    FL_SAVE = 4,
-    FL_APPLY = 8,     // apply the site's K (K_0, or K_0^dagger backwards) after the other actions
-    FL_KDIAG = 32
-};
-
-struct DevOp {
-    int type;      // OP_*
-    int a, b;      // tile positions of q0, q1 (-1 when outside the tile)
-    int qa, qb;    // qubits
-    int mat;       // offset (in float2) of the matrix in the matrix table
-    int site;
-    int flags;     // site flags | event << 8 | spawn count << 16
-};
-
-struct PassArgs {
-    const DevOp* ops;
-    int n_ops;
-    const float2* mats;
-    int n, k, c;
-    int n_events;
-    int local[kMaxTileQ];
-    int nonlocal[kMaxQ];
-    long long n_tiles;
-    const float2* in[3];
-    float2* out[3];
-    float2* const* ckpt;   // phi_s slots
-    float2* spawn[9];
-    double* partials;      // [(event * S + state) * grid + block][8]
-};
-
-// ------------------------------------------------------------------ helpers
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {   // a*b + c
-    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
-}
-__device__ __forceinline__ int insert0(int p, int pos) {
-    return ((p >> pos) << (pos + 1)) | (p & ((1 << pos) - 1));
-}
-
-template <int S>
-struct PassShared {
-    unsigned long long hi_off[1 << (kMaxTileQ - 5)];
-    double acc[kMaxEvents][S][kWarps][8];
-};
-
-template <int S>
-__global__ void __launch_bounds__(kThreads) pass_kernel(const PassArgs P) {
-    extern __shared__ __align__(16) float2 tile[];   // S * 2^k
-    __shared__ PassShared<S> sh;
-    const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    const int k = P.k, c = P.c;
-    const int T = 1 << k;
-    const int cmask = (1 << c) - 1;
-    const int nhi = 1 << (k - c);
-
-    for (int h = tid; h < nhi; h += kThreads) {
-        unsigned long long off = 0;
-        for (int j = 0; j < k - c; ++j)
-            if ((h >> j) & 1) off |= 1ull << P.local[c + j];
-        sh.hi_off[h] = off;
-    }
-    for (int i = tid; i < kMaxEvents * S * kWarps * 8; i += kThreads) (&sh.acc[0][0][0][0])[i] = 0.0;
-    __syncthreads();
-
-    for (long long t = blockIdx.x; t < P.n_tiles; t += gridDim.x) {
-        unsigned long long base = 0;
-        for (int j = 0; j < P.n - k; ++j)
-            if ((t >> j) & 1) base |= 1ull << P.nonlocal[j];
-        auto gaddr = [&](int j) -> unsigned long long { return base | sh.hi_off[j >> c] | (unsigned long long)(j & cmask); };
-
-        // load (2 amplitudes per 16-byte vector; j even so the address is aligned)
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const float4* src = reinterpret_cast<const float4*>(P.in[s]);
-            for (int f = tid; f < (T >> 1); f += kThreads) {
-                int j = f << 1;
-                float4 v = __ldcs(src + (gaddr(j) >> 1));
-                tile[s * T + j] = make_float2(v.x, v.y);
-                tile[s * T + j + 1] = make_float2(v.z, v.w);
-            }
-        }
-        __syncthreads();
-
-        for (int o = 0; o < P.n_ops; ++o) {
-            const DevOp op = P.ops[o];
-            if (op.type == OP_G1) {
-                const float2 m0 = P.mats[op.mat], m1 = P.mats[op.mat + 1];
-                const float2 m2 = P.mats[op.mat + 2], m3 = P.mats[op.mat + 3];
-                const int bit = 1 << op.a;
-                for (int p = tid; p < (T >> 1); p += kThreads) {
-                    int j0 = insert0(p, op.a), j1 = j0 | bit;
-#pragma unroll
-                    for (int s = 0; s < S; ++s) {
-                        float2 x0 = tile[s * T + j0], x1 = tile[s * T + j1];
-                        tile[s * T + j0] = cfma(m0, x0, cmul(m1, x1));
-                        tile[s * T + j1] = cfma(m2, x0, cmul(m3, x1));
-                    }
-                }
-            } else if (op.type == OP_G2) {
-                float2 m[16];
-#pragma unroll
-                for (int e = 0; e < 16; ++e) m[e] = P.mats[op.mat + e];
-                const int lo = min(op.a, op.b), hi = max(op.a, op.b);
-                const int ba = 1 << op.a, bb = 1 << op.b;
-                for (int p = tid; p < (T >> 2); p += kThreads) {
-                    int j = insert0(insert0(p, lo), hi);
-                    int idx[4] = {j, j | bb, j | ba, j | ba | bb};
-#pragma unroll
-                    for (int s = 0; s < S; ++s) {
-                        float2 x[4];
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) x[r] = tile[s * T + idx[r]];
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            float2 y = cmul(m[4 * r], x[0]);
-                            y = cfma(m[4 * r + 1], x[1], y);
-                            y = cfma(m[4 * r + 2], x[2], y);
-                            y = cfma(m[4 * r + 3], x[3], y);
-                            tile[s * T + idx[r]] = y;
-                        }
-                    }
-                }
-            } else if (op.type == OP_D1) {
-                const float2 d0 = P.mats[op.mat], d1 = P.mats[op.mat + 3];
-                if (op.a >= 0) {
-                    for (int j = tid; j < T; j += kThreads) {
-                        float2 d = ((j >> op.a) & 1) ? d1 : d0;
-#pragma unroll
-                        for (int s = 0; s < S; ++s) tile[s * T + j] = cmul(d, tile[s * T + j]);
-                    }
-                } else {
-                    float2 d = ((base >> op.qa) & 1) ? d1 : d0;
-                    for (int j = tid; j < T; j += kThreads)
-#pragma unroll
-                        for (int s = 0; s < S; ++s) tile[s * T + j] = cmul(d, tile[s * T + j]);
-                }
-            } else if (op.type == OP_D2) {
-                float2 d[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) d[e] = P.mats[op.mat + 5 * e];
-                const int fa = (op.a < 0) ? (int)((base >> op.qa) & 1) : -1;
-                const int fb = (op.b < 0) ? (int)((base >> op.qb) & 1) : -1;
-                for (int j = tid; j < T; j += kThreads) {
-                    int b0 = fa >= 0 ? fa : ((j >> op.a) & 1);
-                    int b1 = fb >= 0 ? fb : ((j >> op.b) & 1);
-                    float2 f = d[2 * b0 + b1];
-#pragma unroll
-                    for (int s = 0; s < S; ++s) tile[s * T + j] = cmul(f, tile[s * T + j]);
-                }
-            } else if (op.type == OP_SITE) {
-                const int fl = op.flags & 0xff;
-                const int ev = (op.flags >> 8) & 0xff;
-                const int nspawn = (op.flags >> 16) & 0xff;
-                const int bit = 1 << op.a;
-                const float2 k0 = P.mats[op.mat], k1 = P.mats[op.mat + 1];
-                const float2 k2 = P.mats[op.mat + 2], k3 = P.mats[op.mat + 3];
-                const float2* phi = (fl & FL_REDUCE) ? P.ckpt[op.site] : nullptr;
-                float2* save = (fl & FL_SAVE) ? P.ckpt[op.site] : nullptr;
-                float r[S][8];
-#pragma unroll
-                for (int s = 0; s < S; ++s)
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) r[s][e] = 0.f;
-                for (int p = tid; p < (T >> 1); p += kThreads) {
-                    int j0 = insert0(p, op.a), j1 = j0 | bit;
-                    unsigned long long g0 = gaddr(j0), g1 = gaddr(j1);
-                    float2 f0, f1;
-                    if (fl & FL_REDUCE) {
-                        f0 = __ldcs(phi + g0);
-                        f1 = __ldcs(phi + g1);
-                    }
-#pragma unroll
-                    for (int s = 0; s < S; ++s) {
-                        float2 x0 = tile[s * T + j0], x1 = tile[s * T + j1];
-                        // phi_s excludes the site's own factor: save before applying K_0^dagger
-                        if ((fl & FL_SAVE) && s == 0) {
-                            __stcs(save + g0, x0);
-                            __stcs(save + g1, x1);
-                        }
-                        if (fl & FL_REDUCE) {
-                            // R[a][b] += conj(phi_a) * x_b
-                            r[s][0] += f0.x * x0.x + f0.y * x0.y;  r[s][1] += f0.x * x0.y - f0.y * x0.x;
-                            r[s][2] += f0.x * x1.x + f0.y * x1.y;  r[s][3] += f0.x * x1.y - f0.y * x1.x;
-                            r[s][4] += f1.x * x0.x + f1.y * x0.y;  r[s][5] += f1.x * x0.y - f1.y * x0.x;
-                            r[s][6] += f1.x * x1.x + f1.y * x1.y;  r[s][7] += f1.x * x1.y - f1.y * x1.x;
-                        }
-                        if (fl & FL_SPAWN) {
-                            for (int i = 0; i < nspawn; ++i) {
-                                const float2* K = P.mats + op.mat + 4 * (i + 1);
-                                float2* dst = P.spawn[s * 3 + i];
-                                __stcs(dst + g0, cfma(K[0], x0, cmul(K[1], x1)));
-                                __stcs(dst + g1, cfma(K[2], x0, cmul(K[3], x1)));
-                            }
-                        }
-                        if (fl & FL_APPLY) {
-                            float2 y0, y1;
-                            if (fl & FL_KDIAG) {
-                                y0 = cmul(k0, x0);
-                                y1 = cmul(k3, x1);
-                            } else {
-                                y0 = cfma(k0, x0, cmul(k1, x1));
-                                y1 = cfma(k2, x0, cmul(k3, x1));
-                            }
-                            tile[s * T + j0] = y0;
-                            tile[s * T + j1] = y1;
-                        }
-                    }
-                }
-                if (fl & FL_REDUCE) {
-#pragma unroll
-                    for (int s = 0; s < S; ++s) {
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            float v = r[s][e];
-#pragma unroll
-                            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-                            if (lane == 0) sh.acc[ev][s][warp][e] += (double)v;
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-        }
-
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            float4* dst = reinterpret_cast<float4*>(P.out[s]);
-            for (int f = tid; f < (T >> 1); f += kThreads) {
-                int j = f << 1;
-                float2 a = tile[s * T + j], b = tile[s * T + j + 1];
-                __stcs(dst + (gaddr(j) >> 1), make_float4(a.x, a.y, b.x, b.y));
-            }
-        }
-        __syncthreads();
-    }
-
-    for (int i = tid; i < P.n_events * S * 8; i += kThreads) {
-        int e = i & 7, s = (i >> 3) % S, ev = (i >> 3) / S;
-        double v = 0.0;
-        for (int w = 0; w < kWarps; ++w) v += sh.acc[ev][s][w][e];
-        P.partials[((size_t)(ev * S + s) * gridDim.x + blockIdx.x) * 8 + e] = v;
-    }
-}
-
-// Standalone reduced-matrix kernel (nqs_reduced_matrix and the N = 0 path):
-// grid-stride over amplitude pairs of qubit q.
-__global__ void __launch_bounds__(kThreads) reduce2x2_kernel(const float2* __restrict__ phi,
-                                                             const float2* __restrict__ chi, int n, int q,
-                                                             double* __restrict__ partials) {
-    __shared__ double acc[kWarps][8];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < kWarps * 8) (&acc[0][0])[tid] = 0.0;
-    __syncthreads();
-    const long long npairs = 1ll << (n - 1);
-    const long long bit = 1ll << q;
-    const long long stride = (long long)gridDim.x * kThreads;
-    long long p = (long long)blockIdx.x * kThreads + tid;
-    while (__any_sync(0xffffffffu, p < npairs)) {
-        float r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int it = 0; it < 16 && p < npairs; ++it, p += stride) {
-            long long lo = p & (bit - 1);
-            long long i0 = ((p - lo) << 1) | lo, i1 = i0 | bit;
-            float2 f0 = __ldcs(phi + i0), f1 = __ldcs(phi + i1);
-            float2 x0 = __ldcs(chi + i0), x1 = __ldcs(chi + i1);
-            r[0] += f0.x * x0.x + f0.y * x0.y;  r[1] += f0.x * x0.y - f0.y * x0.x;
-            r[2] += f0.x * x1.x + f0.y * x1.y;  r[3] += f0.x * x1.y - f0.y * x1.x;
-            r[4] += f1.x * x0.x + f1.y * x0.y;  r[5] += f1.x * x0.y - f1.y * x0.x;
-            r[6] += f1.x * x1.x + f1.y * x1.y;  r[7] += f1.x * x1.y - f1.y * x1.x;
-        }
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            float v = r[e];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            if (lane == 0) acc[warp][e] += (double)v;
-        }
-    }
-    __syncthreads();
-    if (tid < 8) {
-        double v = 0.0;
-        for (int w = 0; w < kWarps; ++w) v += acc[w][tid];
-        partials[(size_t)blockIdx.x * 8 + tid] = v;
-    }
-}
-
-// Sum per-block partials of one reduction slot in a fixed order: thread t
-// takes blocks t, t+256, ...; then a fixed tree.
-__device__ void sum_partials(const double* part, int grid, double* R, double* scratch) {
-    const int tid = threadIdx.x;
-    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int b = tid; b < grid; b += kThreads)
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] += part[(size_t)b * 8 + e];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) scratch[e * kThreads + tid] = v[e];
-    __syncthreads();
-    for (int w = kThreads / 2; w > 0; w >>= 1) {
-        if (tid < w)
-#pragma unroll
-            for (int e = 0; e < 8; ++e) scratch[e * kThreads + tid] += scratch[e * kThreads + tid + w];
-        __syncthreads();
-    }
-    if (tid < 8) R[tid] = scratch[tid * kThreads];
-    __syncthreads();
-}
-
-struct FinishDesc {
-    long long rank;   // -1: no term
-    int kmat;         // offset (doubles) of the 2x2 complex128 factor
-    int pad;
-};
-
-// One block per reduction slot (event, state): R from the partials, then
-// X = |sum_ab K[a][b] R[a][b]|^2 for each factor of the slot.
-__global__ void __launch_bounds__(kThreads) finish_kernel(const double* __restrict__ partials, int grid,
-                                                          const FinishDesc* __restrict__ desc,
-                                                          const double* __restrict__ kmats,
-                                                          double* __restrict__ term_vals) {
-    __shared__ double scratch[8 * kThreads];
-    __shared__ double R[8];
-    sum_partials(partials + (size_t)blockIdx.x * grid * 8, grid, R, scratch);
-    if (threadIdx.x < 4) {
-        FinishDesc d = desc[blockIdx.x * 4 + threadIdx.x];
-        if (d.rank >= 0) {
-            const double* K = kmats + d.kmat;
-            double re = 0, im = 0;
-            for (int e = 0; e < 4; ++e) {
-                double kr = K[2 * e], ki = K[2 * e + 1], rr = R[2 * e], ri = R[2 * e + 1];
-                re += kr * rr - ki * ri;
-                im += kr * ri + ki * rr;
-            }
-            term_vals[d.rank] = re * re + im * im;
-        }
-    }
-}
-
-// One block: fixed-order sum of per-block partials into 8 doubles.
-__global__ void __launch_bounds__(kThreads) partials_sum_kernel(const double* __restrict__ part, int grid,
-                                                                double* __restrict__ R) {
-    __shared__ double scratch[8 * kThreads];
-    __shared__ double r[8];
-    sum_partials(part, grid, r, scratch);
-    if (threadIdx.x < 8) R[threadIdx.x] = r[threadIdx.x];
-}
-
-// Neumaier-compensated per-level sums in canonical order, one block.
-__global__ void __launch_bounds__(kThreads) level_sum_kernel(const double* __restrict__ vals,
-                                                             const long long* __restrict__ level_off, int level,
-                                                             nqs_result* __restrict__ res, double bound,
-                                                             long long n_terms) {
-    __shared__ double s_sum[kThreads], s_comp[kThreads];
-    __shared__ double T[NQS_MAX_LEVEL + 1];
-    const int tid = threadIdx.x;
-    for (int u = 0; u <= level; ++u) {
-        long long lo = level_off[u], hi = level_off[u + 1];
-        long long len = hi - lo;
-        long long chunk = (len + kThreads - 1) / kThreads;
-        long long a = lo + chunk * tid, b = min(hi, a + chunk);
-        double sum = 0.0, comp = 0.0;
-        for (long long i = a; i < b; ++i) {
-            double x = vals[i];
-            double t = sum + x;
-            if (fabs(sum) >= fabs(x)) comp += (sum - t) + x;
-            else comp += (x - t) + sum;
-            sum = t;
-        }
-        s_sum[tid] = sum;
-        s_comp[tid] = comp;
-        __syncthreads();
-        if (tid == 0) {
-            double S = 0.0, C = 0.0;
-            for (int i = 0; i < kThreads; ++i) {
-                double x = s_sum[i];
-                double t = S + x;
-                if (fabs(S) >= fabs(x)) C += (S - t) + x;
-                else C += (x - t) + S;
-                S = t;
-                C += s_comp[i];
-            }
-            T[u] = S + C;
-        }
-        __syncthreads();
-    }
-    if (tid == 0) {
-        double S = 0.0, C = 0.0;
-        for (int u = 0; u <= NQS_MAX_LEVEL; ++u) {
-            double x = (u <= level) ? T[u] : 0.0;
-            res->T[u] = x;
-            double t = S + x;
-            if (fabs(S) >= fabs(x)) C += (S - t) + x;
-            else C += (x - t) + S;
-            S = t;
-        }
-        res->F = S + C;
-        res->imag_residual = 0.0;
-        res->n_terms = (uint64_t)n_terms;
-        res->bound = bound;
-        res->level = level;
-        res->status = NQS_OK;
-    }
-}
-
-__global__ void basis_fill_kernel(float2* out, long long dim, unsigned long long bits) {
-    long long stride = (long long)gridDim.x * blockDim.x;
-    float4* o4 = reinterpret_cast<float4*>(out);
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (dim >> 1); i += stride) {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if ((unsigned long long)(2 * i) == bits) v.x = 1.f;
-        if ((unsigned long long)(2 * i + 1) == bits) v.z = 1.f;
-        o4[i] = v;
-    }
-}
 
 // ------------------------------------------------------------------ host side
 namespace {
@@ -470,6 +46,7 @@ struct RunPass {
     std::vector<int> lin;            // linear op index of each device op
     std::vector<int> ev_site;        // site of reduction event e
     int spawn_site = -1;             // site that spawns in this pass (at most one)
+    int phase_off = 0, n_phases = 0; // register-resident phases (device phase buffer)
 };
 
 struct Run {
@@ -483,6 +60,8 @@ struct Launch {
     int S = 1;
     PassArgs args{};
     int op_index = 0;                // offset of the first device op (rebased onto the device table)
+    int phase_index = 0;             // offset of the first phase (register-resident kernel)
+    bool rt = false;                 // register-resident kernel
     int grid = 0;
     size_t smem = 0;
     // finisher
@@ -494,8 +73,6 @@ struct Launch {
     unsigned long long bits = 0;
     double bytes = 0;                // algorithmic bytes (pass kernels)
 };
-
-int blocks_per_sm(int S, size_t smem);
 
 }  // namespace
 
@@ -522,42 +99,19 @@ struct Engine {
     FinishDesc* desc_dev = nullptr;
     double* partials = nullptr;
     double* kmats_dev = nullptr;
+    int* err_dev = nullptr;
     // profiling
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
     std::vector<std::pair<int, double>> ev_used;    // kind, bytes per used pair
     size_t ev_next = 0;
     cudaStream_t last_stream = nullptr;
     bool has_result = false;
+    uint64_t upload_bytes = 0;
 };
 
 namespace {
 
 int cuda_err(cudaError_t e) { return e == cudaSuccess ? NQS_OK : NQS_ERR_CUDA; }
-
-template <int S>
-void set_smem_attr() {
-    static bool done = false;
-    if (!done) {
-        cudaFuncSetAttribute(pass_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             S * (1 << kMaxTileQ) * (int)sizeof(float2));
-        done = true;
-    }
-}
-
-int blocks_per_sm(int S, size_t smem) {
-    int nb = 0;
-    if (S == 1) {
-        set_smem_attr<1>();
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<1>, kThreads, smem);
-    } else if (S == 2) {
-        set_smem_attr<2>();
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<2>, kThreads, smem);
-    } else {
-        set_smem_attr<3>();
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<3>, kThreads, smem);
-    }
-    return std::max(nb, 1);
-}
 
 // Matrix table builder (float2 for sweeps, complex128 for finishers).
 struct Tables {
@@ -577,9 +131,96 @@ struct Tables {
 
 enum RunType { RT_IDEAL, RT_BWD, RT_FWD };
 
+// Group the operations of one pass (execution order) into register phases:
+// a phase gathers consecutive operations whose dense qubits fit in the four
+// register qubits; diagonal operations never constrain it.  Each phase's
+// layout pads the register set with the highest free tile positions, then
+// gives the lane bits to the lowest free position of each residue class
+// mod 5 (those are the bank bits of the swizzled transpose buffer), and the
+// warp bits to the rest.  Operation qubits get their location codes.
+void build_phases(std::vector<DevOp>& dops, int off, int n, int k, std::vector<DevPhase>& out) {
+    std::vector<std::pair<int, int>> ranges;
+    std::vector<std::vector<int>> regs;
+    std::vector<int> cur;
+    int begin = 0;
+    for (int o = 0; o < n; ++o) {
+        const DevOp& d = dops[off + o];
+        std::vector<int> need;
+        if (d.type == OP_G1 || d.type == OP_SITE) need.push_back(d.a);
+        else if (d.type == OP_G2) {
+            need.push_back(d.a);
+            need.push_back(d.b);
+        }
+        std::vector<int> u = cur;
+        for (int q : need)
+            if (std::find(u.begin(), u.end(), q) == u.end()) u.push_back(q);
+        if ((int)u.size() > kRegBits) {
+            ranges.push_back({begin, o});
+            regs.push_back(cur);
+            cur = need;
+            begin = o;
+        } else {
+            cur = u;
+        }
+    }
+    ranges.push_back({begin, n});
+    regs.push_back(cur);
+    for (size_t p = 0; p < ranges.size(); ++p) {
+        std::vector<int> R = regs[p];
+        std::vector<char> used(k, 0);
+        for (int q : R) used[q] = 1;
+        for (int q = k - 1; q >= 0 && (int)R.size() < kRegBits; --q)
+            if (!used[q]) {
+                R.push_back(q);
+                used[q] = 1;
+            }
+        std::sort(R.begin(), R.end());
+        std::vector<int> lanes;
+        bool res_used[5] = {false, false, false, false, false};
+        for (int q = 0; q < k && (int)lanes.size() < 5; ++q)
+            if (!used[q] && !res_used[q % 5]) {
+                lanes.push_back(q);
+                res_used[q % 5] = true;
+            }
+        for (int q : lanes) used[q] = 1;
+        for (int q = 0; q < k && (int)lanes.size() < 5; ++q)
+            if (!used[q]) {
+                lanes.push_back(q);
+                used[q] = 1;
+            }
+        std::sort(lanes.begin(), lanes.end());
+        std::vector<int> warps;
+        for (int q = 0; q < k; ++q)
+            if (!used[q]) warps.push_back(q);
+        DevPhase ph{};
+        int loc[kMaxTileQ];
+        for (int i = 0; i < kRegBits; ++i) {
+            ph.R[i] = (signed char)R[i];
+            loc[R[i]] = i;
+        }
+        for (int i = 0; i < 5; ++i) {
+            ph.L[i] = (signed char)lanes[i];
+            loc[lanes[i]] = LOC_THREAD + i;
+        }
+        for (int i = 0; i < 3; ++i) {
+            ph.W[i] = (signed char)warps[i];
+            loc[warps[i]] = LOC_THREAD + 5 + i;
+        }
+        ph.op_begin = ranges[p].first;
+        ph.op_end = ranges[p].second;
+        for (int o = ph.op_begin; o < ph.op_end; ++o) {
+            DevOp& d = dops[off + o];
+            d.la = d.a >= 0 ? loc[d.a] : LOC_NONLOCAL;
+            d.lb = d.b >= 0 ? loc[d.b] : LOC_NONLOCAL;
+        }
+        out.push_back(ph);
+    }
+}
+
 // Build device ops for one run type over a segmentation.
 Run make_run(const Plan& plan, const std::vector<PassSpec>& segs, RunType rt, bool reduce, bool spawn,
-             bool level0_only, const std::vector<Factors>& fac, Tables& tab, std::vector<DevOp>& dops) {
+             bool level0_only, const std::vector<Factors>& fac, Tables& tab, std::vector<DevOp>& dops,
+             std::vector<DevPhase>& phases, bool rt_kernel) {
     Run run;
     std::vector<int> fwd_mat(plan.ops.size(), -1), bwd_mat(plan.ops.size(), -1);
     for (size_t i = 0; i < plan.ops.size(); ++i) {
@@ -654,6 +295,11 @@ Run make_run(const Plan& plan, const std::vector<PassSpec>& segs, RunType rt, bo
         else
             for (int i = ps.op_end - 1; i >= ps.op_begin; --i) emit(i);
         rp.n_ops = (int)dops.size() - rp.op_off;
+        if (rt_kernel) {
+            rp.phase_off = (int)phases.size();
+            build_phases(dops, rp.op_off, rp.n_ops, plan.k, phases);
+            rp.n_phases = (int)phases.size() - rp.phase_off;
+        }
         return rp;
     };
     if (rt == RT_BWD) {
@@ -677,6 +323,8 @@ struct Builder {
     TermIndex ti;
     Tables tab;
     std::vector<DevOp> dops;
+    std::vector<DevPhase> dphases;
+    bool rt = false;                  // register-resident kernel (tile of exactly 12 qubits)
     std::vector<FinishDesc> descs;
     std::vector<Launch> L;
     size_t partial_doubles = 0;
@@ -695,7 +343,8 @@ struct Builder {
 
     int grid_for(int S, long long tiles) {
         size_t smem = (size_t)S * (1 << plan.k) * sizeof(float2);
-        long long g = (long long)blocks_per_sm(S, smem) * E.sm_count;
+        int per_sm = rt ? sweep_blocks_per_sm(S) : tile_pass_blocks_per_sm(S, smem);
+        long long g = (long long)per_sm * E.sm_count;
         return (int)std::max<long long>(1, std::min<long long>(g, tiles));
     }
 
@@ -723,6 +372,29 @@ struct Builder {
         l.S = S;
         l.args = pass_args(rp, start, S);
         l.op_index = rp.op_off + start;
+        l.rt = rt;
+        if (rt) {
+            if (start == 0) {
+                l.phase_index = rp.phase_off;
+                l.args.n_phases = rp.n_phases;
+            } else {
+                // trimmed phase list for a launch that starts inside the pass
+                l.phase_index = (int)dphases.size();
+                for (int p = 0; p < rp.n_phases; ++p) {
+                    DevPhase ph = dphases[rp.phase_off + p];
+                    if (ph.op_end <= start) continue;
+                    ph.op_begin = std::max(ph.op_begin, start) - start;
+                    ph.op_end = ph.op_end - start;
+                    dphases.push_back(ph);
+                }
+                if ((int)dphases.size() == l.phase_index) {   // nothing left to apply: a plain copy
+                    DevPhase ph = dphases[rp.phase_off + rp.n_phases - 1];
+                    ph.op_begin = ph.op_end = 0;
+                    dphases.push_back(ph);
+                }
+                l.args.n_phases = (int)dphases.size() - l.phase_index;
+            }
+        }
         for (int s = 0; s < S; ++s) {
             l.args.in[s] = in[s];
             l.args.out[s] = out[s];
@@ -880,17 +552,18 @@ static int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_
     for (int s = 0; s < N; ++s) m[s] = h.factors[s].m;
     B.ti.build(m, level);
 
-    // runs
+    // runs: the register-resident kernel needs a tile of exactly 12 qubits
+    B.rt = plan.k == kMaxTileQ;
     bool need_ideal = v->kind == NQS_STATE_IDEAL;
-    if (need_ideal) B.run_ideal = make_run(plan, plan.free_passes, RT_IDEAL, false, false, false, h.factors, B.tab, B.dops);
-    if (N > 0) B.run_bwd = make_run(plan, plan.free_passes, RT_BWD, false, false, false, h.factors, B.tab, B.dops);
+    if (need_ideal) B.run_ideal = make_run(plan, plan.free_passes, RT_IDEAL, false, false, false, h.factors, B.tab, B.dops, B.dphases, B.rt);
+    if (N > 0) B.run_bwd = make_run(plan, plan.free_passes, RT_BWD, false, false, false, h.factors, B.tab, B.dops, B.dphases, B.rt);
     // forward runs per depth d: reduce if d+1 <= level (or level 0 at depth 0), spawn if d+2 <= level
     int depths = std::max(1, level);
     for (int d = 0; d < depths; ++d) {
         bool spawn = d + 2 <= level;
         bool reduce = (level == 0) ? (d == 0) : (d + 1 <= level);
         B.run_fwd.push_back(make_run(plan, spawn ? plan.sitecut_passes : plan.free_passes, RT_FWD, reduce && N > 0,
-                                     spawn, level == 0, h.factors, B.tab, B.dops));
+                                     spawn, level == 0, h.factors, B.tab, B.dops, B.dphases, B.rt));
     }
     // finisher factor table (complex128)
     B.tab.kmats.assign((size_t)std::max(N, 1) * 32, 0.0);
@@ -1052,7 +725,9 @@ static int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_
     size_t off_ops = 0;
     size_t off_mats = align(off_ops + B.dops.size() * sizeof(DevOp) + 1);
     size_t off_ckpt = align(off_mats + B.tab.mats.size() * sizeof(float2) + 1);
-    size_t off_kmat = align(off_ckpt + n_phi * sizeof(float2*));
+    size_t off_phase = align(off_ckpt + n_phi * sizeof(float2*));
+    size_t off_err = align(off_phase + B.dphases.size() * sizeof(DevPhase) + 1);
+    size_t off_kmat = align(off_err + sizeof(int));
     size_t off_desc = align(off_kmat + B.tab.kmats.size() * sizeof(double));
     size_t off_part = align(off_desc + B.descs.size() * sizeof(FinishDesc) + 1);
     size_t off_vals = align(off_part + std::max<size_t>(B.partial_doubles, 8) * sizeof(double));
@@ -1070,6 +745,8 @@ static int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_
     B.ckpt_dev = (float2**)(ab + off_ckpt);
     float2* mats_dev = (float2*)(ab + off_mats);
     float2** ckpt_dev = (float2**)(ab + off_ckpt);
+    DevPhase* phases_dev = (DevPhase*)(ab + off_phase);
+    E.err_dev = (int*)(ab + off_err);
     E.kmats_dev = (double*)(ab + off_kmat);
     E.desc_dev = (FinishDesc*)(ab + off_desc);
     E.partials = (double*)(ab + off_part);
@@ -1081,12 +758,15 @@ static int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_
     std::vector<long long> loff(level + 2);
     for (int u = 0; u <= level + 1; ++u) loff[u] = (long long)B.ti.level_offset[u];
     int rc = NQS_OK;
+    E.upload_bytes = 0;
     auto up = [&](void* dst, const void* src, size_t bytes) {
         if (bytes && rc == NQS_OK) rc = cuda_err(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+        E.upload_bytes += bytes;
     };
     up(dops_dev, B.dops.data(), B.dops.size() * sizeof(DevOp));
     up(mats_dev, B.tab.mats.data(), B.tab.mats.size() * sizeof(float2));
     up(ckpt_dev, B.phi.data(), n_phi * sizeof(float2*));
+    up(phases_dev, B.dphases.data(), B.dphases.size() * sizeof(DevPhase));
     up(E.kmats_dev, B.tab.kmats.data(), B.tab.kmats.size() * sizeof(double));
     up(E.desc_dev, B.descs.data(), B.descs.size() * sizeof(FinishDesc));
     up(E.level_off_dev, loff.data(), loff.size() * sizeof(long long));
@@ -1101,6 +781,8 @@ static int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_
     for (auto& l : B.L) {
         if (l.kind != L_PASS) continue;
         l.args.ops = dops_dev + l.op_index;
+        l.args.phases = l.rt ? phases_dev + l.phase_index : nullptr;
+        l.args.err = E.err_dev;
         l.args.mats = mats_dev;
         l.args.ckpt = ckpt_dev;
         l.args.partials = E.partials;
@@ -1132,20 +814,21 @@ static int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_
 }
 
 static int launch_pass(const Launch& l, cudaStream_t st) {
-    if (l.S == 1) pass_kernel<1><<<l.grid, kThreads, l.smem, st>>>(l.args);
-    else if (l.S == 2) pass_kernel<2><<<l.grid, kThreads, l.smem, st>>>(l.args);
-    else pass_kernel<3><<<l.grid, kThreads, l.smem, st>>>(l.args);
-    return cuda_err(cudaGetLastError());
+    if (l.rt) return cuda_err(launch_sweep(l.S, l.grid, l.args, st));
+    return cuda_err(launch_tile_pass(l.S, l.grid, l.smem, l.args, st));
 }
 
 static int run_schedule(Handle& h, Engine& E, cudaStream_t st) {
     const long long dim = 1ll << h.plan.n;
     int rc = NQS_OK;
     int fill_grid = (int)std::max<long long>(1, std::min<long long>(E.sm_count * 8, dim / 512));
+    rc = cuda_err(cudaMemsetAsync(E.err_dev, 0, sizeof(int), st));
+    if (rc != NQS_OK) return rc;
     for (const Launch& l : E.launches) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         int kind = (l.kind == L_PASS) ? 0 : (l.kind == L_FINISH || l.kind == L_SUM || l.kind == L_REDUCE2) ? 1 : 2;
-        if (h.profiling) {
+        const bool timed = h.profiling && l.kind != L_COPY;
+        if (timed) {
             if (E.ev_next >= E.ev_pool.size()) {
                 cudaEvent_t a, b;
                 cudaEventCreate(&a);
@@ -1161,28 +844,24 @@ static int run_schedule(Handle& h, Engine& E, cudaStream_t st) {
         switch (l.kind) {
             case L_PASS: rc = launch_pass(l, st); break;
             case L_FINISH:
-                finish_kernel<<<l.n_red, kThreads, 0, st>>>(E.partials, l.fin_grid, E.desc_dev + l.desc_off, E.kmats_dev,
-                                                            E.term_vals);
-                rc = cuda_err(cudaGetLastError());
+                rc = cuda_err(launch_finish(E.partials, l.fin_grid, E.desc_dev + l.desc_off, E.kmats_dev,
+                                            E.term_vals, l.n_red, st));
                 break;
             case L_FILL:
-                basis_fill_kernel<<<fill_grid, kThreads, 0, st>>>(l.dst, dim, l.bits);
-                rc = cuda_err(cudaGetLastError());
+                rc = cuda_err(launch_basis_fill(l.dst, dim, l.bits, fill_grid, st));
                 break;
             case L_COPY:
                 rc = cuda_err(cudaMemcpyAsync(l.dst, l.src, dim * sizeof(float2), cudaMemcpyDeviceToDevice, st));
                 break;
             case L_REDUCE2:
-                reduce2x2_kernel<<<l.grid, kThreads, 0, st>>>(l.src, l.dst, h.plan.n, 0, E.partials);
-                rc = cuda_err(cudaGetLastError());
+                rc = cuda_err(launch_reduce2x2(l.src, l.dst, h.plan.n, 0, E.partials, l.grid, st));
                 break;
             case L_SUM:
-                level_sum_kernel<<<1, kThreads, 0, st>>>(E.term_vals, E.level_off_dev, E.eff_level, E.res_dev, E.bound,
-                                                         E.n_terms);
-                rc = cuda_err(cudaGetLastError());
+                rc = cuda_err(launch_level_sum(E.term_vals, E.level_off_dev, E.eff_level, E.res_dev, E.bound,
+                                               E.n_terms, E.err_dev, st));
                 break;
         }
-        if (h.profiling) cudaEventRecord(e1, st);
+        if (timed) cudaEventRecord(e1, st);
         if (rc != NQS_OK) return rc;
     }
     return rc;
@@ -1258,6 +937,15 @@ void engine_destroy(Handle& h) {
     h.eng = nullptr;
 }
 
+uint64_t engine_upload_bytes(const Handle& h) { return h.eng ? h.eng->upload_bytes : 0; }
+
+uint64_t engine_launches_per_call(const Handle& h) {
+    if (!h.eng) return 0;
+    uint64_t n = 0;
+    for (const auto& l : h.eng->launches) n += (l.kind != L_COPY) ? 1 : 0;
+    return n;
+}
+
 uint64_t engine_workspace_bytes(const Handle& h) {
     return h.eng ? (uint64_t)(h.eng->buf_bytes + h.eng->aux_bytes) : 0;
 }
@@ -1290,10 +978,9 @@ int engine_reduced_matrix(const void* phi, const void* chi, int n, int qubit, do
     cudaStream_t st = (cudaStream_t)stream;
     double* part = (double*)scratch;
     double* R = part + (size_t)grid * 8;
-    reduce2x2_kernel<<<grid, kThreads, 0, st>>>((const float2*)phi, (const float2*)chi, n, qubit, part);
-    if (cudaGetLastError() != cudaSuccess) return NQS_ERR_CUDA;
-    partials_sum_kernel<<<1, kThreads, 0, st>>>(part, grid, R);
-    if (cudaGetLastError() != cudaSuccess) return NQS_ERR_CUDA;
+    if (launch_reduce2x2((const float2*)phi, (const float2*)chi, n, qubit, part, grid, st) != cudaSuccess)
+        return NQS_ERR_CUDA;
+    if (launch_partials_sum(part, grid, R, st) != cudaSuccess) return NQS_ERR_CUDA;
     if (cudaMemcpyAsync(R_out, R, 8 * sizeof(double), cudaMemcpyDefault, st) != cudaSuccess) return NQS_ERR_CUDA;
     return NQS_OK;
 }

@@ -117,6 +117,8 @@ int engine_fidelity(Handle& h, const nqs_state* psi, const nqs_state* v, int lev
 int engine_term_values(Handle& h, double* out, size_t cap, size_t* count);
 void engine_destroy(Handle& h);
 uint64_t engine_workspace_bytes(const Handle& h);
+uint64_t engine_upload_bytes(const Handle& h);
+uint64_t engine_launches_per_call(const Handle& h);
 int engine_reduced_matrix(const void* phi, const void* chi, int n, int qubit, double* R_out,
                           void* scratch, size_t scratch_bytes, void* stream);
 size_t engine_reduced_matrix_scratch_bytes(int n);

@@ -60,7 +60,8 @@ class nqs_result(ctypes.Structure):
 class nqs_info(ctypes.Structure):
     _fields_ = [("n_qubits", ctypes.c_int32), ("n_gates", ctypes.c_int32), ("n_sites", ctypes.c_int32),
                 ("n_ops", ctypes.c_int32), ("n_passes", ctypes.c_int32), ("tile_qubits", ctypes.c_int32),
-                ("workspace_bytes", ctypes.c_uint64)]
+                ("workspace_bytes", ctypes.c_uint64), ("upload_bytes", ctypes.c_uint64),
+                ("launches_per_call", ctypes.c_uint64)]
 
 
 class nqs_kernel_stats(ctypes.Structure):
