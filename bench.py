@@ -42,6 +42,8 @@ WORKLOADS = {
                   "p~U[1e-4,1e-2], v=U|psi>, level 2"),
     "grid20_l2": ("c2_grid20", 2, "4x5 grid depth 16 (444 gates), 20 AD(1e-3)*PD(1e-3), v bitstring, level 2"),
     "line6_l4": ("c1_line6", 4, "line n=6 depth 8 (68 gates), 4 depolarizing p=1e-3, level 4 (exact)"),
+    # small profiling case: same structure as the 30-qubit workload, 128 MiB states
+    "qaoa24_l1": ("qaoa24", 1, "QAOA MaxCut n=24 (3-regular, p=4), 20 depolarizing, v=U|psi>, level 1"),
 }
 
 
@@ -60,6 +62,8 @@ def parse_args():
 def make_workload(name):
     import workloads as W
     gen, level, desc = WORKLOADS[name]
+    if gen == "qaoa24":
+        return W.qaoa_workload(24, 3, 20, 4, "ideal", "qaoa24"), level, desc
     return getattr(W, gen)(), level, desc
 
 

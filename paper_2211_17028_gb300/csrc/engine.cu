@@ -60,7 +60,7 @@ struct Launch {
     int S = 1;
     PassArgs args{};
     int op_index = 0;                // offset of the first device op (rebased onto the device table)
-    int phase_index = 0;             // offset of the first phase (register-resident kernel)
+    int prog_index = 0;              // offset (16-byte words) of the launch's program
     bool rt = false;                 // register-resident kernel
     int grid = 0;
     size_t smem = 0;
@@ -131,14 +131,23 @@ struct Tables {
 
 enum RunType { RT_IDEAL, RT_BWD, RT_FWD };
 
-// Group the operations of one pass (execution order) into register phases:
-// a phase gathers consecutive operations whose dense qubits fit in the four
-// register qubits; diagonal operations never constrain it.  Each phase's
-// layout pads the register set with the highest free tile positions, then
-// gives the lane bits to the lowest free position of each residue class
-// mod 5 (those are the bank bits of the swizzled transpose buffer), and the
-// warp bits to the rest.  Operation qubits get their location codes.
-void build_phases(std::vector<DevOp>& dops, int off, int n, int k, std::vector<DevPhase>& out) {
+// Program of one register-resident launch, appended to `prog` (16-byte
+// words): the phases, one 16-byte record per operation, then the matrices.
+// The operations (execution order) are grouped into phases: a phase gathers
+// consecutive operations whose dense qubits fit in the RB register qubits;
+// diagonal operations never constrain it.  Each phase pads its register set
+// with the highest free tile positions, gives the lane bits to the lowest
+// free position of each residue class mod 5 (the bank bits of the swizzled
+// transpose buffer) and the warp bits to the rest.  Returns the offsets
+// (in words) of the operations and matrices and the phase count.
+struct ProgInfo {
+    int words_begin = 0, n_words = 0, ops_word = 0, mats_word = 0, n_phases = 0;
+};
+
+ProgInfo build_program(const std::vector<DevOp>& dops, int off, int n, int RB, const Tables& tab,
+                       std::vector<uint4>& prog) {
+    const int k = kMaxTileQ;
+    const int WB = k - RB - 5;
     std::vector<std::pair<int, int>> ranges;
     std::vector<std::vector<int>> regs;
     std::vector<int> cur;
@@ -154,7 +163,7 @@ void build_phases(std::vector<DevOp>& dops, int off, int n, int k, std::vector<D
         std::vector<int> u = cur;
         for (int q : need)
             if (std::find(u.begin(), u.end(), q) == u.end()) u.push_back(q);
-        if ((int)u.size() > kRegBits) {
+        if ((int)u.size() > RB) {
             ranges.push_back({begin, o});
             regs.push_back(cur);
             cur = need;
@@ -165,11 +174,15 @@ void build_phases(std::vector<DevOp>& dops, int off, int n, int k, std::vector<D
     }
     ranges.push_back({begin, n});
     regs.push_back(cur);
+
+    std::vector<DevPhase> phases;
+    std::vector<OpRec> recs(n);
+    std::vector<float2> mats;
     for (size_t p = 0; p < ranges.size(); ++p) {
         std::vector<int> R = regs[p];
         std::vector<char> used(k, 0);
         for (int q : R) used[q] = 1;
-        for (int q = k - 1; q >= 0 && (int)R.size() < kRegBits; --q)
+        for (int q = k - 1; q >= 0 && (int)R.size() < RB; --q)
             if (!used[q]) {
                 R.push_back(q);
                 used[q] = 1;
@@ -194,7 +207,7 @@ void build_phases(std::vector<DevOp>& dops, int off, int n, int k, std::vector<D
             if (!used[q]) warps.push_back(q);
         DevPhase ph{};
         int loc[kMaxTileQ];
-        for (int i = 0; i < kRegBits; ++i) {
+        for (int i = 0; i < RB; ++i) {
             ph.R[i] = (signed char)R[i];
             loc[R[i]] = i;
         }
@@ -202,25 +215,51 @@ void build_phases(std::vector<DevOp>& dops, int off, int n, int k, std::vector<D
             ph.L[i] = (signed char)lanes[i];
             loc[lanes[i]] = LOC_THREAD + i;
         }
-        for (int i = 0; i < 3; ++i) {
+        for (int i = 0; i < WB; ++i) {
             ph.W[i] = (signed char)warps[i];
             loc[warps[i]] = LOC_THREAD + 5 + i;
         }
         ph.op_begin = ranges[p].first;
         ph.op_end = ranges[p].second;
+        phases.push_back(ph);
         for (int o = ph.op_begin; o < ph.op_end; ++o) {
-            DevOp& d = dops[off + o];
-            d.la = d.a >= 0 ? loc[d.a] : LOC_NONLOCAL;
-            d.lb = d.b >= 0 ? loc[d.b] : LOC_NONLOCAL;
+            const DevOp& d = dops[off + o];
+            OpRec& r = recs[o];
+            r = OpRec{};
+            r.type = (unsigned char)d.type;
+            r.la = (unsigned char)(d.a >= 0 ? loc[d.a] : 0xff);
+            r.lb = (unsigned char)(d.b >= 0 ? loc[d.b] : 0xff);
+            r.flags = (unsigned char)(d.flags & 0xff);
+            r.qa = (unsigned char)(d.qa >= 0 ? d.qa : 0xff);
+            r.qb = (unsigned char)(d.qb >= 0 ? d.qb : 0xff);
+            r.ev = (unsigned char)((d.flags >> 8) & 0xff);
+            r.nspawn = (unsigned char)((d.flags >> 16) & 0xff);
+            r.site = (unsigned short)(d.site >= 0 ? d.site : 0);
+            int cnt = (d.type == OP_G2 || d.type == OP_D2) ? 16 : 4;
+            if (d.type == OP_SITE && (d.flags & FL_SPAWN)) cnt = 16;
+            r.mat = (unsigned short)mats.size();
+            for (int e = 0; e < cnt; ++e) mats.push_back(tab.mats[d.mat + e]);
         }
-        out.push_back(ph);
     }
+    ProgInfo info;
+    info.words_begin = (int)prog.size();
+    info.n_phases = (int)phases.size();
+    static_assert(sizeof(DevPhase) == 32 && sizeof(OpRec) == 16, "program record sizes");
+    const uint4* pw = reinterpret_cast<const uint4*>(phases.data());
+    prog.insert(prog.end(), pw, pw + 2 * phases.size());
+    info.ops_word = (int)prog.size() - info.words_begin;
+    const uint4* ow = reinterpret_cast<const uint4*>(recs.data());
+    prog.insert(prog.end(), ow, ow + recs.size());
+    info.mats_word = (int)prog.size() - info.words_begin;
+    if (mats.size() & 1) mats.push_back(make_float2(0.f, 0.f));
+    const uint4* mw = reinterpret_cast<const uint4*>(mats.data());
+    prog.insert(prog.end(), mw, mw + mats.size() / 2);
+    info.n_words = (int)prog.size() - info.words_begin;
+    return info;
 }
 
-// Build device ops for one run type over a segmentation.
 Run make_run(const Plan& plan, const std::vector<PassSpec>& segs, RunType rt, bool reduce, bool spawn,
-             bool level0_only, const std::vector<Factors>& fac, Tables& tab, std::vector<DevOp>& dops,
-             std::vector<DevPhase>& phases, bool rt_kernel) {
+             bool level0_only, const std::vector<Factors>& fac, Tables& tab, std::vector<DevOp>& dops) {
     Run run;
     std::vector<int> fwd_mat(plan.ops.size(), -1), bwd_mat(plan.ops.size(), -1);
     for (size_t i = 0; i < plan.ops.size(); ++i) {
@@ -295,11 +334,6 @@ Run make_run(const Plan& plan, const std::vector<PassSpec>& segs, RunType rt, bo
         else
             for (int i = ps.op_end - 1; i >= ps.op_begin; --i) emit(i);
         rp.n_ops = (int)dops.size() - rp.op_off;
-        if (rt_kernel) {
-            rp.phase_off = (int)phases.size();
-            build_phases(dops, rp.op_off, rp.n_ops, plan.k, phases);
-            rp.n_phases = (int)phases.size() - rp.phase_off;
-        }
         return rp;
     };
     if (rt == RT_BWD) {
@@ -323,7 +357,7 @@ struct Builder {
     TermIndex ti;
     Tables tab;
     std::vector<DevOp> dops;
-    std::vector<DevPhase> dphases;
+    std::vector<uint4> prog;          // programs of the register-resident launches
     bool rt = false;                  // register-resident kernel (tile of exactly 12 qubits)
     std::vector<FinishDesc> descs;
     std::vector<Launch> L;
@@ -341,9 +375,14 @@ struct Builder {
         dim = 1ll << plan.n;
     }
 
-    int grid_for(int S, long long tiles) {
-        size_t smem = (size_t)S * (1 << plan.k) * sizeof(float2);
-        int per_sm = rt ? sweep_blocks_per_sm(S) : tile_pass_blocks_per_sm(S, smem);
+    int grid_for(int S, long long tiles, int prog_words, int n_events) {
+        int per_sm;
+        if (rt) {
+            per_sm = sweep_blocks_per_sm(S, sweep_smem_bytes(S, prog_words, n_events));
+        } else {
+            size_t smem = (size_t)S * (1 << plan.k) * sizeof(float2);
+            per_sm = tile_pass_blocks_per_sm(S, smem);
+        }
         long long g = (long long)per_sm * E.sm_count;
         return (int)std::max<long long>(1, std::min<long long>(g, tiles));
     }
@@ -374,33 +413,19 @@ struct Builder {
         l.op_index = rp.op_off + start;
         l.rt = rt;
         if (rt) {
-            if (start == 0) {
-                l.phase_index = rp.phase_off;
-                l.args.n_phases = rp.n_phases;
-            } else {
-                // trimmed phase list for a launch that starts inside the pass
-                l.phase_index = (int)dphases.size();
-                for (int p = 0; p < rp.n_phases; ++p) {
-                    DevPhase ph = dphases[rp.phase_off + p];
-                    if (ph.op_end <= start) continue;
-                    ph.op_begin = std::max(ph.op_begin, start) - start;
-                    ph.op_end = ph.op_end - start;
-                    dphases.push_back(ph);
-                }
-                if ((int)dphases.size() == l.phase_index) {   // nothing left to apply: a plain copy
-                    DevPhase ph = dphases[rp.phase_off + rp.n_phases - 1];
-                    ph.op_begin = ph.op_end = 0;
-                    dphases.push_back(ph);
-                }
-                l.args.n_phases = (int)dphases.size() - l.phase_index;
-            }
+            ProgInfo pi = build_program(dops, rp.op_off + start, rp.n_ops - start, sweep_reg_bits(S), tab, prog);
+            l.prog_index = pi.words_begin;
+            l.args.prog_words = pi.n_words;
+            l.args.ops_word = pi.ops_word;
+            l.args.mats_word = pi.mats_word;
+            l.args.n_phases = pi.n_phases;
         }
         for (int s = 0; s < S; ++s) {
             l.args.in[s] = in[s];
             l.args.out[s] = out[s];
         }
         for (int i = 0; i < n_spawn; ++i) l.args.spawn[i] = spawn[i];
-        l.grid = grid_for(S, l.args.n_tiles);
+        l.grid = grid_for(S, l.args.n_tiles, l.args.prog_words, l.args.n_events);
         l.smem = (size_t)S * (1 << plan.k) * sizeof(float2);
         partial_doubles = std::max(partial_doubles, (size_t)std::max(1, l.args.n_events) * S * l.grid * 8);
         // algorithmic bytes: state load + store, phi reads, checkpoint and spawn writes
@@ -555,15 +580,15 @@ static int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_
     // runs: the register-resident kernel needs a tile of exactly 12 qubits
     B.rt = plan.k == kMaxTileQ;
     bool need_ideal = v->kind == NQS_STATE_IDEAL;
-    if (need_ideal) B.run_ideal = make_run(plan, plan.free_passes, RT_IDEAL, false, false, false, h.factors, B.tab, B.dops, B.dphases, B.rt);
-    if (N > 0) B.run_bwd = make_run(plan, plan.free_passes, RT_BWD, false, false, false, h.factors, B.tab, B.dops, B.dphases, B.rt);
+    if (need_ideal) B.run_ideal = make_run(plan, plan.free_passes, RT_IDEAL, false, false, false, h.factors, B.tab, B.dops);
+    if (N > 0) B.run_bwd = make_run(plan, plan.free_passes, RT_BWD, false, false, false, h.factors, B.tab, B.dops);
     // forward runs per depth d: reduce if d+1 <= level (or level 0 at depth 0), spawn if d+2 <= level
     int depths = std::max(1, level);
     for (int d = 0; d < depths; ++d) {
         bool spawn = d + 2 <= level;
         bool reduce = (level == 0) ? (d == 0) : (d + 1 <= level);
         B.run_fwd.push_back(make_run(plan, spawn ? plan.sitecut_passes : plan.free_passes, RT_FWD, reduce && N > 0,
-                                     spawn, level == 0, h.factors, B.tab, B.dops, B.dphases, B.rt));
+                                     spawn, level == 0, h.factors, B.tab, B.dops));
     }
     // finisher factor table (complex128)
     B.tab.kmats.assign((size_t)std::max(N, 1) * 32, 0.0);
@@ -726,7 +751,7 @@ static int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_
     size_t off_mats = align(off_ops + B.dops.size() * sizeof(DevOp) + 1);
     size_t off_ckpt = align(off_mats + B.tab.mats.size() * sizeof(float2) + 1);
     size_t off_phase = align(off_ckpt + n_phi * sizeof(float2*));
-    size_t off_err = align(off_phase + B.dphases.size() * sizeof(DevPhase) + 1);
+    size_t off_err = align(off_phase + B.prog.size() * sizeof(uint4) + 1);
     size_t off_kmat = align(off_err + sizeof(int));
     size_t off_desc = align(off_kmat + B.tab.kmats.size() * sizeof(double));
     size_t off_part = align(off_desc + B.descs.size() * sizeof(FinishDesc) + 1);
@@ -745,7 +770,7 @@ static int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_
     B.ckpt_dev = (float2**)(ab + off_ckpt);
     float2* mats_dev = (float2*)(ab + off_mats);
     float2** ckpt_dev = (float2**)(ab + off_ckpt);
-    DevPhase* phases_dev = (DevPhase*)(ab + off_phase);
+    uint4* prog_dev = (uint4*)(ab + off_phase);
     E.err_dev = (int*)(ab + off_err);
     E.kmats_dev = (double*)(ab + off_kmat);
     E.desc_dev = (FinishDesc*)(ab + off_desc);
@@ -766,7 +791,7 @@ static int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_
     up(dops_dev, B.dops.data(), B.dops.size() * sizeof(DevOp));
     up(mats_dev, B.tab.mats.data(), B.tab.mats.size() * sizeof(float2));
     up(ckpt_dev, B.phi.data(), n_phi * sizeof(float2*));
-    up(phases_dev, B.dphases.data(), B.dphases.size() * sizeof(DevPhase));
+    up(prog_dev, B.prog.data(), B.prog.size() * sizeof(uint4));
     up(E.kmats_dev, B.tab.kmats.data(), B.tab.kmats.size() * sizeof(double));
     up(E.desc_dev, B.descs.data(), B.descs.size() * sizeof(FinishDesc));
     up(E.level_off_dev, loff.data(), loff.size() * sizeof(long long));
@@ -781,7 +806,7 @@ static int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_
     for (auto& l : B.L) {
         if (l.kind != L_PASS) continue;
         l.args.ops = dops_dev + l.op_index;
-        l.args.phases = l.rt ? phases_dev + l.phase_index : nullptr;
+        l.args.prog = l.rt ? prog_dev + l.prog_index : nullptr;
         l.args.err = E.err_dev;
         l.args.mats = mats_dev;
         l.args.ckpt = ckpt_dev;

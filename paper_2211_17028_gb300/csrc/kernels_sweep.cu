@@ -1,20 +1,26 @@
-// Register-resident tile sweep for sm_103a (tile = 12 qubits = 4096 amplitudes
-// per state, 256 threads, 16 amplitudes per thread per state).
+// Register-resident tile sweep for sm_103a: a tile is 12 qubits (4096
+// amplitudes) of each of S states; each thread holds E = 2^RB amplitudes per
+// state in registers (RB "register qubits"), so a block has 4096 / E threads.
 //
-// The next tile of every state is prefetched with TMA bulk copies
-// (cp.async.bulk, 256-byte runs of the 5 contiguous low qubits) into a
-// shared-memory staging buffer, completion tracked by an mbarrier, while the
-// current tile is processed in registers.  The pass's fused operations are
-// grouped into phases; in a phase four of the tile's qubits are "register
-// qubits" (the 16 amplitudes a thread holds differ only in them), so every
-// dense one- or two-qubit operation of the phase is applied without touching
-// shared memory.  Between phases the tile is re-laid out through a second,
-// XOR-swizzled shared-memory buffer.  Diagonal operations on any qubit --
-// including qubits outside the tile -- are folded into a per-thread factor
-// table (one complex factor per register qubit value plus a scalar) and
-// applied once, before the next dense operation.  Site operations (checkpoint
-// save, reduction against phi_site, spawning K_i x, applying K_0) act on a
-// register qubit and read / write HBM directly.
+// * Prefetch: the next tile of every state is brought into a shared-memory
+//   staging buffer by TMA bulk copies (cp.async.bulk, one 256-byte run of
+//   the 5 contiguous low qubits per copy) whose completion is tracked by an
+//   mbarrier, while the current tile is processed in registers.  Every wait
+//   on the mbarrier is bounded; a wait that gives up sets the device status
+//   word, lets the copies in flight land and returns.
+// * Program: the launch's phases, 16-byte operation records and matrices are
+//   copied into shared memory once per block.
+// * Phases: in a phase RB of the tile's qubits are register qubits, so every
+//   dense one- or two-qubit operation of the phase is applied without
+//   touching shared memory; between phases the tile is re-laid out through
+//   a second, XOR-swizzled shared-memory buffer.
+// * Diagonal operations on any qubit, inside or outside the tile, are folded
+//   into a per-thread factor (a scalar plus one pair of factors per register
+//   qubit) and applied once, before the next dense operation.
+// * Site operations (checkpoint save, reduction against phi_site, spawning
+//   K_i x, applying K_0) act on a register qubit and read / write HBM
+//   directly; reductions go FP32 per thread -> FP32 warp shuffle -> FP64
+//   per-warp slot, then per-block partials summed in a fixed order later.
 #include "sweep_types.h"
 #include "nqs_internal.h"
 
@@ -71,40 +77,38 @@ __device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
 }
 
 // ---- dense operations on register qubits -----------------------------------
-template <int I, int S>
-__device__ __forceinline__ void g1_reg(float2 (&x)[S][kRegElems], float2 m0, float2 m1, float2 m2, float2 m3) {
+template <int I, int S, int E>
+__device__ __forceinline__ void g1_reg(float2 (&x)[S][E], float2 m0, float2 m1, float2 m2, float2 m3) {
 #pragma unroll
-    for (int r = 0; r < kRegElems; ++r) {
+    for (int r = 0; r < E; ++r) {
         if (r & (1 << I)) continue;
         const int r1 = r | (1 << I);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            float2 a = x[s][r], b = x[s][r1];
+            const float2 a = x[s][r], b = x[s][r1];
             x[s][r] = cfma(m0, a, cmul(m1, b));
             x[s][r1] = cfma(m2, a, cmul(m3, b));
         }
     }
 }
 
-template <int S>
-__device__ __forceinline__ void g1_dispatch(int i, float2 (&x)[S][kRegElems], const float2* m) {
+template <int S, int E, int RB>
+__device__ __forceinline__ void g1_dispatch(int i, float2 (&x)[S][E], const float2* m) {
     const float2 m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3];
-    switch (i) {
-        case 0: g1_reg<0>(x, m0, m1, m2, m3); break;
-        case 1: g1_reg<1>(x, m0, m1, m2, m3); break;
-        case 2: g1_reg<2>(x, m0, m1, m2, m3); break;
-        default: g1_reg<3>(x, m0, m1, m2, m3); break;
-    }
+    if (i == 0) g1_reg<0>(x, m0, m1, m2, m3);
+    else if (i == 1) g1_reg<1>(x, m0, m1, m2, m3);
+    else if (i == 2) g1_reg<2>(x, m0, m1, m2, m3);
+    else if constexpr (RB > 3) g1_reg<3>(x, m0, m1, m2, m3);
 }
 
-// 4x4 matrix indexed 2*b(first) + b(second); first on register bit I0
-template <int I0, int I1, int S>
-__device__ __forceinline__ void g2_reg(float2 (&x)[S][kRegElems], const float2* mg) {
+// 4x4 matrix indexed 2*b(first) + b(second); first qubit on register bit I0
+template <int I0, int I1, int S, int E>
+__device__ __forceinline__ void g2_reg(float2 (&x)[S][E], const float2* mg) {
     float2 m[16];
 #pragma unroll
     for (int e = 0; e < 16; ++e) m[e] = mg[e];
 #pragma unroll
-    for (int r = 0; r < kRegElems; ++r) {
+    for (int r = 0; r < E; ++r) {
         if (r & ((1 << I0) | (1 << I1))) continue;
         const int idx[4] = {r, r | (1 << I1), r | (1 << I0), r | (1 << I0) | (1 << I1)};
 #pragma unroll
@@ -124,77 +128,43 @@ __device__ __forceinline__ void g2_reg(float2 (&x)[S][kRegElems], const float2* 
     }
 }
 
-template <int S>
-__device__ __forceinline__ void g2_dispatch(int i0, int i1, float2 (&x)[S][kRegElems], const float2* m) {
+template <int S, int E, int RB>
+__device__ __forceinline__ void g2_dispatch(int i0, int i1, float2 (&x)[S][E], const float2* m) {
     switch (i0 * 4 + i1) {
         case 1: g2_reg<0, 1>(x, m); break;
         case 2: g2_reg<0, 2>(x, m); break;
-        case 3: g2_reg<0, 3>(x, m); break;
         case 4: g2_reg<1, 0>(x, m); break;
         case 6: g2_reg<1, 2>(x, m); break;
-        case 7: g2_reg<1, 3>(x, m); break;
         case 8: g2_reg<2, 0>(x, m); break;
         case 9: g2_reg<2, 1>(x, m); break;
-        case 11: g2_reg<2, 3>(x, m); break;
-        case 12: g2_reg<3, 0>(x, m); break;
-        case 13: g2_reg<3, 1>(x, m); break;
-        case 14: g2_reg<3, 2>(x, m); break;
-        default: break;
+        default:
+            if constexpr (RB > 3) {
+                switch (i0 * 4 + i1) {
+                    case 3: g2_reg<0, 3>(x, m); break;
+                    case 7: g2_reg<1, 3>(x, m); break;
+                    case 11: g2_reg<2, 3>(x, m); break;
+                    case 12: g2_reg<3, 0>(x, m); break;
+                    case 13: g2_reg<3, 1>(x, m); break;
+                    case 14: g2_reg<3, 2>(x, m); break;
+                    default: break;
+                }
+            }
+            break;
     }
-}
-
-// ---- pending diagonal factor ------------------------------------------------
-struct Diag {
-    float2 sc;
-    float2 h[kRegBits][2];
-    int mask;
-    bool pend;
-};
-
-__device__ __forceinline__ void diag_reset(Diag& d) {
-    d.sc = make_float2(1.f, 0.f);
-#pragma unroll
-    for (int i = 0; i < kRegBits; ++i) d.h[i][0] = d.h[i][1] = make_float2(1.f, 0.f);
-    d.mask = 0;
-    d.pend = false;
-}
-
-__device__ __forceinline__ void diag_mul_reg(Diag& d, int i, float2 f0, float2 f1) {
-    switch (i) {
-        case 0: d.h[0][0] = cmul(d.h[0][0], f0); d.h[0][1] = cmul(d.h[0][1], f1); break;
-        case 1: d.h[1][0] = cmul(d.h[1][0], f0); d.h[1][1] = cmul(d.h[1][1], f1); break;
-        case 2: d.h[2][0] = cmul(d.h[2][0], f0); d.h[2][1] = cmul(d.h[2][1], f1); break;
-        default: d.h[3][0] = cmul(d.h[3][0], f0); d.h[3][1] = cmul(d.h[3][1], f1); break;
-    }
-    d.mask |= 1 << i;
-    d.pend = true;
-}
-
-template <int S>
-__device__ __forceinline__ void diag_flush(Diag& d, float2 (&x)[S][kRegElems]) {
-    if (!d.pend) return;
-#pragma unroll
-    for (int r = 0; r < kRegElems; ++r) {
-        float2 f = d.sc;
-#pragma unroll
-        for (int i = 0; i < kRegBits; ++i)
-            if (d.mask & (1 << i)) f = cmul(f, d.h[i][(r >> i) & 1]);
-#pragma unroll
-        for (int s = 0; s < S; ++s) x[s][r] = cmul(f, x[s][r]);
-    }
-    diag_reset(d);
 }
 
 // ---- layouts ----------------------------------------------------------------
+template <int RB>
 struct Layout {
     int jT;                          // tile index bits owned by the thread (lanes, warps)
-    int jR[kRegBits];                // tile index bit of each register qubit
+    int jR[RB];                      // tile index bit of each register qubit
     unsigned long long gT;           // the same in global index bits
-    unsigned long long gR[kRegBits];
+    unsigned long long gR[RB];
 };
 
-__device__ __forceinline__ Layout make_layout(const DevPhase& ph, const int* local, int tid) {
-    Layout L;
+template <int RB>
+__device__ __forceinline__ void make_layout(Layout<RB>& L, const DevPhase& ph, const int* local, int tid) {
+    constexpr int WB = kMaxTileQ - RB - 5;
     L.jT = 0;
     L.gT = 0;
 #pragma unroll
@@ -204,50 +174,49 @@ __device__ __forceinline__ Layout make_layout(const DevPhase& ph, const int* loc
             L.gT |= 1ull << local[ph.L[i]];
         }
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < WB; ++i)
         if ((tid >> (5 + i)) & 1) {
             L.jT |= 1 << ph.W[i];
             L.gT |= 1ull << local[ph.W[i]];
         }
 #pragma unroll
-    for (int i = 0; i < kRegBits; ++i) {
+    for (int i = 0; i < RB; ++i) {
         L.jR[i] = 1 << ph.R[i];
         L.gR[i] = 1ull << local[ph.R[i]];
     }
-    return L;
 }
 
-__device__ __forceinline__ int jr_of(const Layout& L, int r) {
+template <int RB>
+__device__ __forceinline__ int jr_of(const Layout<RB>& L, int r) {
     int j = 0;
 #pragma unroll
-    for (int i = 0; i < kRegBits; ++i)
+    for (int i = 0; i < RB; ++i)
         if (r & (1 << i)) j |= L.jR[i];
     return j;
 }
 
-__device__ __forceinline__ unsigned long long gr_of(const Layout& L, int r) {
+template <int RB>
+__device__ __forceinline__ unsigned long long gr_of(const Layout<RB>& L, int r) {
     unsigned long long g = 0;
 #pragma unroll
-    for (int i = 0; i < kRegBits; ++i)
+    for (int i = 0; i < RB; ++i)
         if (r & (1 << i)) g |= L.gR[i];
     return g;
 }
 
-// bit of a qubit for this thread: location code from the phase layout
+// bit of a qubit that is not a register qubit: a thread bit, or (code 0xff)
+// a bit of the tile's base index
 __device__ __forceinline__ int const_bit(int loc, int qubit, int tid, unsigned long long base) {
-    return (loc >= LOC_THREAD) ? ((tid >> (loc - LOC_THREAD)) & 1) : (int)((base >> qubit) & 1);
+    return (loc != 0xff) ? ((tid >> (loc - LOC_THREAD)) & 1) : (int)((base >> qubit) & 1);
 }
 
-// ---- site operation on register qubit I ---------------------------------------
-template <int I, int S>
-__device__ __forceinline__ void site_reg(const PassArgs& P, const DevOp& op, float2 (&x)[S][kRegElems],
-                                         const Layout& L, unsigned long long base, double (*acc)[kWarps][8],
-                                         int lane, int warp) {
-    const int fl = op.flags & 0xff;
-    const int ev = (op.flags >> 8) & 0xff;
-    const int nspawn = (op.flags >> 16) & 0xff;
-    const float2* km = P.mats + op.mat;
-    const float2 k0 = km[0], k1 = km[1], k2 = km[2], k3 = km[3];
+template <int I, int S, int E, int RB>
+__device__ __forceinline__ void site_reg(const PassArgs& P, const OpRec& op, const float2* m, float2 (&x)[S][E],
+                                         const Layout<RB>& L, unsigned long long base, double* acc, int lane,
+                                         int warp) {
+    constexpr int NW = (kT >> RB) / 32;
+    const int fl = op.flags;
+    const float2 k0 = m[0], k1 = m[1], k2 = m[2], k3 = m[3];
     const float2* phi = (fl & FL_REDUCE) ? P.ckpt[op.site] : nullptr;
     float2* save = (fl & FL_SAVE) ? P.ckpt[op.site] : nullptr;
     float rr[S][8];
@@ -256,7 +225,7 @@ __device__ __forceinline__ void site_reg(const PassArgs& P, const DevOp& op, flo
 #pragma unroll
         for (int e = 0; e < 8; ++e) rr[s][e] = 0.f;
 #pragma unroll
-    for (int r = 0; r < kRegElems; ++r) {
+    for (int r = 0; r < E; ++r) {
         if (r & (1 << I)) continue;
         const int r1 = r | (1 << I);
         const unsigned long long g0 = base | L.gT | gr_of(L, r);
@@ -280,8 +249,8 @@ __device__ __forceinline__ void site_reg(const PassArgs& P, const DevOp& op, flo
                 rr[s][6] += f1.x * b.x + f1.y * b.y;  rr[s][7] += f1.x * b.y - f1.y * b.x;
             }
             if (fl & FL_SPAWN) {
-                for (int i = 0; i < nspawn; ++i) {
-                    const float2* K = km + 4 * (i + 1);
+                for (int i = 0; i < op.nspawn; ++i) {
+                    const float2* K = m + 4 * (i + 1);
                     float2* dst = P.spawn[s * 3 + i];
                     __stcs(dst + g0, cfma(K[0], a, cmul(K[1], b)));
                     __stcs(dst + g1, cfma(K[2], a, cmul(K[3], b)));
@@ -306,45 +275,51 @@ __device__ __forceinline__ void site_reg(const PassArgs& P, const DevOp& op, flo
                 float v = rr[s][e];
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-                if (lane == 0) acc[ev * S + s][warp][e] += (double)v;
+                if (lane == 0) acc[((op.ev * S + s) * NW + warp) * 8 + e] += (double)v;
             }
     }
 }
 
-template <int S>
-__device__ __forceinline__ void site_dispatch(int i, const PassArgs& P, const DevOp& op, float2 (&x)[S][kRegElems],
-                                              const Layout& L, unsigned long long base, double (*acc)[kWarps][8],
-                                              int lane, int warp) {
-    switch (i) {
-        case 0: site_reg<0>(P, op, x, L, base, acc, lane, warp); break;
-        case 1: site_reg<1>(P, op, x, L, base, acc, lane, warp); break;
-        case 2: site_reg<2>(P, op, x, L, base, acc, lane, warp); break;
-        default: site_reg<3>(P, op, x, L, base, acc, lane, warp); break;
-    }
+template <int S, int E, int RB>
+__device__ __forceinline__ void site_dispatch(int i, const PassArgs& P, const OpRec& op, const float2* m,
+                                              float2 (&x)[S][E], const Layout<RB>& L, unsigned long long base,
+                                              double* acc, int lane, int warp) {
+    if (i == 0) site_reg<0>(P, op, m, x, L, base, acc, lane, warp);
+    else if (i == 1) site_reg<1>(P, op, m, x, L, base, acc, lane, warp);
+    else if (i == 2) site_reg<2>(P, op, m, x, L, base, acc, lane, warp);
+    else if constexpr (RB > 3) site_reg<3>(P, op, m, x, L, base, acc, lane, warp);
 }
 
-template <int S>
-__global__ void __launch_bounds__(kThreads, 1) sweep_kernel(const PassArgs P) {
+template <int S, int RB>
+__global__ void __launch_bounds__(kT >> RB, (S == 1 ? 2 : 1)) sweep_kernel(const PassArgs P) {
+    constexpr int E = 1 << RB;
+    constexpr int NT = kT >> RB;
+    constexpr int NW = NT / 32;
     extern __shared__ __align__(128) unsigned char dyn[];
-    float2* pf = reinterpret_cast<float2*>(dyn);                          // [S][kT], TMA destination
-    float* tr = reinterpret_cast<float*>(dyn + (size_t)S * kT * sizeof(float2));   // [S][2][kT], swizzled
+    float2* pf = reinterpret_cast<float2*>(dyn);                                  // [S][kT] TMA staging
+    float* tr = reinterpret_cast<float*>(dyn + (size_t)S * kT * sizeof(float2));   // [S][2][kT] swizzled
+    uint4* prog = reinterpret_cast<uint4*>(dyn + (size_t)S * kT * 16);              // phases, ops, matrices
+    double* acc = reinterpret_cast<double*>(prog + P.prog_words);                   // [ev][S][NW][8]
     __shared__ __align__(8) uint64_t bar;
     __shared__ unsigned long long hi_off[kChunks];
-    __shared__ double acc[kMaxEvents * S][kWarps][8];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int h = tid; h < kChunks; h += kThreads) {
+    for (int i = tid; i < P.prog_words; i += NT) prog[i] = P.prog[i];
+    for (int h = tid; h < kChunks; h += NT) {
         unsigned long long off = 0;
         for (int j = 0; j < kMaxTileQ - 5; ++j)
             if ((h >> j) & 1) off |= 1ull << P.local[5 + j];
         hi_off[h] = off;
     }
-    for (int i = tid; i < kMaxEvents * S * kWarps * 8; i += kThreads) (&acc[0][0][0])[i] = 0.0;
+    for (int i = tid; i < P.n_events * S * NW * 8; i += NT) acc[i] = 0.0;
     if (tid == 0) {
         mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    const DevPhase* phases = reinterpret_cast<const DevPhase*>(prog);
+    const OpRec* ops = reinterpret_cast<const OpRec*>(prog + P.ops_word);
+    const float2* mats = reinterpret_cast<const float2*>(prog + P.mats_word);
 
     auto tile_base = [&](long long t) {
         unsigned long long b = 0;
@@ -352,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_kernel(const PassArgs P) {
             if ((t >> j) & 1) b |= 1ull << P.nonlocal[j];
         return b;
     };
-    auto prefetch = [&](long long t) {   // called by warp 0
+    auto prefetch = [&](long long t) {   // warp 0
         const unsigned long long b = tile_base(t);
         if (lane == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -369,9 +344,8 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_kernel(const PassArgs P) {
     if (t < P.n_tiles && warp == 0) prefetch(t);
     uint32_t parity = 0;
     bool failed = false;
-    float2 x[S][kRegElems];
-    Diag dg;
-    diag_reset(dg);
+    float2 x[S][E];
+    Layout<RB> L;
 
     for (; t < P.n_tiles; t += gridDim.x) {
         const unsigned long long base = tile_base(t);
@@ -381,152 +355,180 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_kernel(const PassArgs P) {
             break;
         }
         parity ^= 1u;
-
-        DevPhase ph = P.phases[0];
-        Layout L = make_layout(ph, P.local, tid);
+        make_layout<RB>(L, phases[0], P.local, tid);
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
-            for (int r = 0; r < kRegElems; ++r) x[s][r] = pf[s * kT + (L.jT | jr_of(L, r))];
+            for (int r = 0; r < E; ++r) x[s][r] = pf[s * kT + (L.jT | jr_of(L, r))];
         __syncthreads();   // the staging buffer is free again
         if (warp == 0 && t + gridDim.x < P.n_tiles) prefetch(t + gridDim.x);
 
+        // pending diagonal factor: scalar + per-register-qubit pairs
+        float2 dsc = make_float2(1.f, 0.f);
+        float2 dh[RB][2];
+#pragma unroll
+        for (int i = 0; i < RB; ++i) dh[i][0] = dh[i][1] = make_float2(1.f, 0.f);
+        int dmask = 0;
+        bool dpend = false;
+        auto flush = [&]() {
+            if (!dpend) return;
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                float2 f = dsc;
+#pragma unroll
+                for (int i = 0; i < RB; ++i)
+                    if (dmask & (1 << i)) f = cmul(f, dh[i][(r >> i) & 1]);
+#pragma unroll
+                for (int s = 0; s < S; ++s) x[s][r] = cmul(f, x[s][r]);
+            }
+            dsc = make_float2(1.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < RB; ++i) dh[i][0] = dh[i][1] = make_float2(1.f, 0.f);
+            dmask = 0;
+            dpend = false;
+        };
+        auto dmul = [&](int i, float2 f0, float2 f1) {
+#pragma unroll
+            for (int k = 0; k < RB; ++k)
+                if (k == i) {
+                    dh[k][0] = cmul(dh[k][0], f0);
+                    dh[k][1] = cmul(dh[k][1], f1);
+                }
+            dmask |= 1 << i;
+            dpend = true;
+        };
+
         for (int p = 0; p < P.n_phases; ++p) {
             if (p > 0) {
-                // re-layout through the swizzled transpose buffer
 #pragma unroll
                 for (int s = 0; s < S; ++s)
 #pragma unroll
-                    for (int r = 0; r < kRegElems; ++r) {
+                    for (int r = 0; r < E; ++r) {
                         const int j = swz(L.jT | jr_of(L, r));
                         tr[(2 * s) * kT + j] = x[s][r].x;
                         tr[(2 * s + 1) * kT + j] = x[s][r].y;
                     }
                 __syncthreads();
-                ph = P.phases[p];
-                L = make_layout(ph, P.local, tid);
+                make_layout<RB>(L, phases[p], P.local, tid);
 #pragma unroll
                 for (int s = 0; s < S; ++s)
 #pragma unroll
-                    for (int r = 0; r < kRegElems; ++r) {
+                    for (int r = 0; r < E; ++r) {
                         const int j = swz(L.jT | jr_of(L, r));
                         x[s][r] = make_float2(tr[(2 * s) * kT + j], tr[(2 * s + 1) * kT + j]);
                     }
                 __syncthreads();
             }
-            for (int o = ph.op_begin; o < ph.op_end; ++o) {
-                const DevOp op = P.ops[o];
+            const int ob = phases[p].op_begin, oe = phases[p].op_end;
+            for (int o = ob; o < oe; ++o) {
+                const OpRec op = ops[o];
+                const float2* m = mats + op.mat;
                 if (op.type == OP_G1) {
-                    diag_flush(dg, x);
-                    g1_dispatch(op.la, x, P.mats + op.mat);
-                } else if (op.type == OP_G2) {
-                    diag_flush(dg, x);
-                    g2_dispatch(op.la, op.lb, x, P.mats + op.mat);
+                    flush();
+                    g1_dispatch<S, E, RB>(op.la, x, m);
                 } else if (op.type == OP_D1) {
-                    const float2 d0 = P.mats[op.mat], d1 = P.mats[op.mat + 3];
-                    if (op.la >= 0 && op.la < kRegBits) {
-                        diag_mul_reg(dg, op.la, d0, d1);
+                    if (op.la < RB) {
+                        dmul(op.la, m[0], m[3]);
                     } else {
-                        dg.sc = cmul(dg.sc, const_bit(op.la, op.qa, tid, base) ? d1 : d0);
-                        dg.pend = true;
+                        dsc = cmul(dsc, const_bit(op.la, op.qa, tid, base) ? m[3] : m[0]);
+                        dpend = true;
                     }
                 } else if (op.type == OP_D2) {
-                    float2 d[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) d[e] = P.mats[op.mat + 5 * e];
-                    const bool ra = op.la >= 0 && op.la < kRegBits;
-                    const bool rb = op.lb >= 0 && op.lb < kRegBits;
+                    const bool ra = op.la < RB, rb = op.lb < RB;
                     if (ra && rb) {
-                        // both qubits in registers: apply now (diagonals commute)
 #pragma unroll
-                        for (int r = 0; r < kRegElems; ++r) {
-                            const float2 f = d[2 * ((r >> op.la) & 1) + ((r >> op.lb) & 1)];
+                        for (int r = 0; r < E; ++r) {
+                            const float2 f = m[5 * (2 * ((r >> op.la) & 1) + ((r >> op.lb) & 1))];
 #pragma unroll
                             for (int s = 0; s < S; ++s) x[s][r] = cmul(f, x[s][r]);
                         }
                     } else if (ra) {
                         const int c = const_bit(op.lb, op.qb, tid, base);
-                        diag_mul_reg(dg, op.la, d[c], d[2 + c]);
+                        dmul(op.la, m[5 * c], m[5 * (2 + c)]);
                     } else if (rb) {
                         const int c = const_bit(op.la, op.qa, tid, base);
-                        diag_mul_reg(dg, op.lb, d[2 * c], d[2 * c + 1]);
+                        dmul(op.lb, m[5 * (2 * c)], m[5 * (2 * c + 1)]);
                     } else {
                         const int c0 = const_bit(op.la, op.qa, tid, base);
                         const int c1 = const_bit(op.lb, op.qb, tid, base);
-                        dg.sc = cmul(dg.sc, d[2 * c0 + c1]);
-                        dg.pend = true;
+                        dsc = cmul(dsc, m[5 * (2 * c0 + c1)]);
+                        dpend = true;
                     }
+                } else if (op.type == OP_G2) {
+                    flush();
+                    g2_dispatch<S, E, RB>(op.la, op.lb, x, m);
                 } else if (op.type == OP_SITE) {
-                    diag_flush(dg, x);
-                    site_dispatch(op.la, P, op, x, L, base, acc, lane, warp);
+                    flush();
+                    site_dispatch<S, E, RB>(op.la, P, op, m, x, L, base, acc, lane, warp);
                 }
             }
-            diag_flush(dg, x);
+            flush();
         }
 
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
-            for (int r = 0; r < kRegElems; ++r) __stcs(P.out[s] + (base | L.gT | gr_of(L, r)), x[s][r]);
+            for (int r = 0; r < E; ++r) __stcs(P.out[s] + (base | L.gT | gr_of(L, r)), x[s][r]);
     }
 
     if (failed) {
         if (tid == 0) atomicExch(P.err, NQS_ERR_DEVICE_TIMEOUT);
-        // let copies still in flight land before the block's shared memory goes away
-        mbar_wait_bounded(&bar, parity);
+        mbar_wait_bounded(&bar, parity);   // let copies still in flight land
         return;
     }
     __syncthreads();
-    for (int i = tid; i < P.n_events * S * 8; i += kThreads) {
+    for (int i = tid; i < P.n_events * S * 8; i += NT) {
         const int e = i & 7, s = (i >> 3) % S, ev = (i >> 3) / S;
         double v = 0.0;
-        for (int w = 0; w < kWarps; ++w) v += acc[ev * S + s][w][e];
+        for (int w = 0; w < NW; ++w) v += acc[((ev * S + s) * NW + w) * 8 + e];
         P.partials[((size_t)(ev * S + s) * gridDim.x + blockIdx.x) * 8 + e] = v;
     }
 }
 
-template <int S>
-void set_attr() {
-    static bool done = false;
-    if (!done) {
-        cudaFuncSetAttribute(sweep_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem_bytes(S));
-        done = true;
-    }
+template <int S, int RB>
+size_t smem_for(int prog_words, int n_events) {
+    constexpr int NW = (kT >> RB) / 32;
+    return (size_t)S * kT * 16 + (size_t)prog_words * 16 + (size_t)n_events * S * NW * 8 * sizeof(double);
+}
+
+template <int S, int RB>
+cudaError_t launch_t(int grid, const PassArgs& P, cudaStream_t st) {
+    const size_t smem = smem_for<S, RB>(P.prog_words, P.n_events);
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<S, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    sweep_kernel<S, RB><<<grid, kT >> RB, smem, st>>>(P);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t sweep_smem_bytes(int S) { return (size_t)S * kT * (sizeof(float2) + 2 * sizeof(float)); }
+int sweep_reg_bits(int S) { return S == 1 ? 4 : 3; }
 
-int sweep_blocks_per_sm(int S) {
+int sweep_blocks_per_sm(int S, size_t smem) {
     int nb = 0;
-    const size_t smem = sweep_smem_bytes(S);
     if (S == 1) {
-        set_attr<1>();
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<1>, kThreads, smem);
+        cudaFuncSetAttribute(sweep_kernel<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<1, 4>, kT >> 4, smem);
     } else if (S == 2) {
-        set_attr<2>();
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<2>, kThreads, smem);
+        cudaFuncSetAttribute(sweep_kernel<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<2, 3>, kT >> 3, smem);
     } else {
-        set_attr<3>();
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<3>, kThreads, smem);
+        cudaFuncSetAttribute(sweep_kernel<3, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<3, 3>, kT >> 3, smem);
     }
     return nb > 0 ? nb : 1;
 }
 
+size_t sweep_smem_bytes(int S, int prog_words, int n_events) {
+    if (S == 1) return smem_for<1, 4>(prog_words, n_events);
+    if (S == 2) return smem_for<2, 3>(prog_words, n_events);
+    return smem_for<3, 3>(prog_words, n_events);
+}
+
 cudaError_t launch_sweep(int S, int grid, const PassArgs& P, cudaStream_t st) {
-    const size_t smem = sweep_smem_bytes(S);
-    if (S == 1) {
-        set_attr<1>();
-        sweep_kernel<1><<<grid, kThreads, smem, st>>>(P);
-    } else if (S == 2) {
-        set_attr<2>();
-        sweep_kernel<2><<<grid, kThreads, smem, st>>>(P);
-    } else {
-        set_attr<3>();
-        sweep_kernel<3><<<grid, kThreads, smem, st>>>(P);
-    }
-    return cudaGetLastError();
+    if (S == 1) return launch_t<1, 4>(grid, P, st);
+    if (S == 2) return launch_t<2, 3>(grid, P, st);
+    return launch_t<3, 3>(grid, P, st);
 }
 
 }  // namespace nqs

@@ -48,15 +48,27 @@ struct DevOp {
 struct DevPhase {
     signed char R[kRegBits];
     signed char L[5];
-    signed char W[3];
-    int op_begin, op_end;   // indices into the launch's op array
+    signed char W[4];
+    signed char pad[3];
+    int op_begin, op_end;   // indices into the launch's op records
+    int pad2[2];
+};
+
+// Compact operation record of the register-resident kernel (16 bytes).
+struct OpRec {
+    unsigned char type, la, lb, flags;   // la, lb: location codes (register bit, LOC_THREAD + bit, 0xff outside)
+    unsigned char qa, qb, ev, nspawn;    // qubits; reduction event; spawned factors
+    unsigned short site, mat;            // site index; matrix offset (float2) in the program
+    unsigned int pad;
 };
 
 struct PassArgs {
     const DevOp* ops;
     int n_ops;
-    const DevPhase* phases;   // register-resident kernel only
+    const DevPhase* phases;   // shared-memory tile kernel: unused
     int n_phases;
+    const uint4* prog;        // register-resident kernel: phases, op records, matrices
+    int prog_words, ops_word, mats_word;
     const float2* mats;
     int n, k, c;
     int n_events;
@@ -93,8 +105,9 @@ __device__ __forceinline__ int insert0(int p, int pos) {
 int tile_pass_blocks_per_sm(int S, size_t smem);
 cudaError_t launch_tile_pass(int S, int grid, size_t smem, const PassArgs& P, cudaStream_t st);
 // register-resident kernel with TMA prefetch (tile width exactly 12 qubits)
-int sweep_blocks_per_sm(int S);
-size_t sweep_smem_bytes(int S);
+int sweep_reg_bits(int S);
+int sweep_blocks_per_sm(int S, size_t smem);
+size_t sweep_smem_bytes(int S, int prog_words, int n_events);
 cudaError_t launch_sweep(int S, int grid, const PassArgs& P, cudaStream_t st);
 // reductions, finishers, fills
 cudaError_t launch_reduce2x2(const float2* phi, const float2* chi, int n, int q, double* partials, int grid,
