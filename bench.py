@@ -44,6 +44,7 @@ WORKLOADS = {
     "line6_l4": ("c1_line6", 4, "line n=6 depth 8 (68 gates), 4 depolarizing p=1e-3, level 4 (exact)"),
     # small profiling case: same structure as the 30-qubit workload, 128 MiB states
     "qaoa24_l1": ("qaoa24", 1, "QAOA MaxCut n=24 (3-regular, p=4), 20 depolarizing, v=U|psi>, level 1"),
+    "qaoa24_l2": ("qaoa24", 2, "QAOA MaxCut n=24 (3-regular, p=4), 20 depolarizing, v=U|psi>, level 2"),
 }
 
 

@@ -62,6 +62,7 @@ struct Launch {
     int op_index = 0;                // offset of the first device op (rebased onto the device table)
     int prog_index = 0;              // offset (16-byte words) of the launch's program
     bool rt = false;                 // register-resident kernel
+    int rb = 4;                      // its register qubits
     int grid = 0;
     size_t smem = 0;
     // finisher
@@ -375,10 +376,10 @@ struct Builder {
         dim = 1ll << plan.n;
     }
 
-    int grid_for(int S, long long tiles, int prog_words, int n_events) {
+    int grid_for(int S, int RB, long long tiles, int prog_words, int n_events) {
         int per_sm;
         if (rt) {
-            per_sm = sweep_blocks_per_sm(S, sweep_smem_bytes(S, prog_words, n_events));
+            per_sm = sweep_blocks_per_sm(S, RB, sweep_smem_bytes(S, RB, prog_words, n_events));
         } else {
             size_t smem = (size_t)S * (1 << plan.k) * sizeof(float2);
             per_sm = tile_pass_blocks_per_sm(S, smem);
@@ -413,7 +414,8 @@ struct Builder {
         l.op_index = rp.op_off + start;
         l.rt = rt;
         if (rt) {
-            ProgInfo pi = build_program(dops, rp.op_off + start, rp.n_ops - start, sweep_reg_bits(S), tab, prog);
+            l.rb = sweep_reg_bits(S);
+            ProgInfo pi = build_program(dops, rp.op_off + start, rp.n_ops - start, l.rb, tab, prog);
             l.prog_index = pi.words_begin;
             l.args.prog_words = pi.n_words;
             l.args.ops_word = pi.ops_word;
@@ -425,7 +427,7 @@ struct Builder {
             l.args.out[s] = out[s];
         }
         for (int i = 0; i < n_spawn; ++i) l.args.spawn[i] = spawn[i];
-        l.grid = grid_for(S, l.args.n_tiles, l.args.prog_words, l.args.n_events);
+        l.grid = grid_for(S, l.rb, l.args.n_tiles, l.args.prog_words, l.args.n_events);
         l.smem = (size_t)S * (1 << plan.k) * sizeof(float2);
         partial_doubles = std::max(partial_doubles, (size_t)std::max(1, l.args.n_events) * S * l.grid * 8);
         // algorithmic bytes: state load + store, phi reads, checkpoint and spawn writes
@@ -839,7 +841,7 @@ static int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_
 }
 
 static int launch_pass(const Launch& l, cudaStream_t st) {
-    if (l.rt) return cuda_err(launch_sweep(l.S, l.grid, l.args, st));
+    if (l.rt) return cuda_err(launch_sweep(l.S, l.rb, l.grid, l.args, st));
     return cuda_err(launch_tile_pass(l.S, l.grid, l.smem, l.args, st));
 }
 

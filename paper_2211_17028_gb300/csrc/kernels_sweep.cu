@@ -21,6 +21,8 @@
 //   K_i x, applying K_0) act on a register qubit and read / write HBM
 //   directly; reductions go FP32 per thread -> FP32 warp shuffle -> FP64
 //   per-warp slot, then per-block partials summed in a fixed order later.
+#include <cstdlib>
+
 #include "sweep_types.h"
 #include "nqs_internal.h"
 
@@ -158,6 +160,7 @@ template <int RB>
 struct Layout {
     int jT;                          // tile index bits owned by the thread (lanes, warps)
     int jR[RB];                      // tile index bit of each register qubit
+    int sT, sR[RB];                  // swz(jT), swz(jR[i]): swz is XOR-linear in the index bits
     unsigned long long gT;           // the same in global index bits
     unsigned long long gR[RB];
 };
@@ -183,7 +186,18 @@ __device__ __forceinline__ void make_layout(Layout<RB>& L, const DevPhase& ph, c
     for (int i = 0; i < RB; ++i) {
         L.jR[i] = 1 << ph.R[i];
         L.gR[i] = 1ull << local[ph.R[i]];
+        L.sR[i] = swz(L.jR[i]);
     }
+    L.sT = swz(L.jT);
+}
+
+template <int RB>
+__device__ __forceinline__ int sr_of(const Layout<RB>& L, int r) {
+    int j = L.sT;
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+        if (r & (1 << i)) j ^= L.sR[i];
+    return j;
 }
 
 template <int RB>
@@ -268,15 +282,49 @@ __device__ __forceinline__ void site_reg(const PassArgs& P, const OpRec& op, con
         }
     }
     if (fl & FL_REDUCE) {
+        // reduce-scatter over the warp: after halving steps 16, 8, 4 lane l
+        // holds the warp sum (over lanes with equal l & 7... completed by
+        // steps 2, 1) of component l & 7 in v[0]
 #pragma unroll
-        for (int s = 0; s < S; ++s)
+        for (int s = 0; s < S; ++s) {
+            float v[8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                float v = rr[s][e];
+            for (int e = 0; e < 8; ++e) v[e] = rr[s][e];
+            // step 16: lanes with bit 4 set keep components 4..7, others 0..3
+            {
+                const bool hi = lane & 16;
 #pragma unroll
-                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-                if (lane == 0) acc[((op.ev * S + s) * NW + warp) * 8 + e] += (double)v;
+                for (int e = 0; e < 4; ++e) {
+                    const float send = hi ? v[e] : v[e + 4];
+                    const float keep = hi ? v[e + 4] : v[e];
+                    v[e] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                }
             }
+            // step 8: keep 2 of the 4
+            {
+                const bool hi = lane & 8;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const float send = hi ? v[e] : v[e + 2];
+                    const float keep = hi ? v[e + 2] : v[e];
+                    v[e] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                }
+            }
+            // step 4: keep 1 of the 2
+            {
+                const bool hi = lane & 4;
+                const float send = hi ? v[0] : v[1];
+                const float keep = hi ? v[1] : v[0];
+                v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+            }
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+            // lane bits 4, 3, 2 select the component: ((l>>4)&1)*4 + ((l>>3)&1)*2 + ((l>>2)&1)
+            if ((lane & 3) == 0) {
+                const int e = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                acc[((op.ev * S + s) * NW + warp) * 8 + e] += (double)v[0];
+            }
+        }
     }
 }
 
@@ -327,21 +375,21 @@ __global__ void __launch_bounds__(kT >> RB, (S == 1 ? 2 : 1)) sweep_kernel(const
             if ((t >> j) & 1) b |= 1ull << P.nonlocal[j];
         return b;
     };
-    auto prefetch = [&](long long t) {   // warp 0
+    // every thread issues its share of the copies (no warp arrives late at
+    // the next barrier); the mbarrier phase cannot complete before thread 0's
+    // arrive.expect_tx, whatever order the copies land in
+    auto prefetch = [&](long long t) {
         const unsigned long long b = tile_base(t);
-        if (lane == 0) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive_expect_tx(&bar, (uint32_t)(S * kT * sizeof(float2)));
-        }
-        __syncwarp();
-        for (int q = lane; q < S * kChunks; q += 32) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (tid == 0) mbar_arrive_expect_tx(&bar, (uint32_t)(S * kT * sizeof(float2)));
+        for (int q = tid; q < S * kChunks; q += NT) {
             const int s = q / kChunks, h = q % kChunks;
             bulk_copy_g2s(pf + s * kT + h * kChunk, P.in[s] + (b | hi_off[h]), kChunk * sizeof(float2), &bar);
         }
     };
 
     long long t = blockIdx.x;
-    if (t < P.n_tiles && warp == 0) prefetch(t);
+    if (t < P.n_tiles) prefetch(t);
     uint32_t parity = 0;
     bool failed = false;
     float2 x[S][E];
@@ -361,7 +409,7 @@ __global__ void __launch_bounds__(kT >> RB, (S == 1 ? 2 : 1)) sweep_kernel(const
 #pragma unroll
             for (int r = 0; r < E; ++r) x[s][r] = pf[s * kT + (L.jT | jr_of(L, r))];
         __syncthreads();   // the staging buffer is free again
-        if (warp == 0 && t + gridDim.x < P.n_tiles) prefetch(t + gridDim.x);
+        if (t + gridDim.x < P.n_tiles) prefetch(t + gridDim.x);
 
         // pending diagonal factor: scalar + per-register-qubit pairs
         float2 dsc = make_float2(1.f, 0.f);
@@ -400,11 +448,12 @@ __global__ void __launch_bounds__(kT >> RB, (S == 1 ? 2 : 1)) sweep_kernel(const
 
         for (int p = 0; p < P.n_phases; ++p) {
             if (p > 0) {
+                flush();
 #pragma unroll
                 for (int s = 0; s < S; ++s)
 #pragma unroll
                     for (int r = 0; r < E; ++r) {
-                        const int j = swz(L.jT | jr_of(L, r));
+                        const int j = sr_of(L, r);
                         tr[(2 * s) * kT + j] = x[s][r].x;
                         tr[(2 * s + 1) * kT + j] = x[s][r].y;
                     }
@@ -414,7 +463,7 @@ __global__ void __launch_bounds__(kT >> RB, (S == 1 ? 2 : 1)) sweep_kernel(const
                 for (int s = 0; s < S; ++s)
 #pragma unroll
                     for (int r = 0; r < E; ++r) {
-                        const int j = swz(L.jT | jr_of(L, r));
+                        const int j = sr_of(L, r);
                         x[s][r] = make_float2(tr[(2 * s) * kT + j], tr[(2 * s + 1) * kT + j]);
                     }
                 __syncthreads();
@@ -424,8 +473,29 @@ __global__ void __launch_bounds__(kT >> RB, (S == 1 ? 2 : 1)) sweep_kernel(const
                 const OpRec op = ops[o];
                 const float2* m = mats + op.mat;
                 if (op.type == OP_G1) {
-                    flush();
-                    g1_dispatch<S, E, RB>(op.la, x, m);
+                    // the pending factor on this register qubit is absorbed into the
+                    // matrix columns; the rest of the pending diagonal commutes
+                    float2 mm[4] = {m[0], m[1], m[2], m[3]};
+                    if (dpend) {   // the pending scalar multiplies every amplitude the gate touches
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) mm[e] = cmul(mm[e], dsc);
+                        dsc = make_float2(1.f, 0.f);
+                        dpend = dmask != 0;
+                    }
+                    if (dmask & (1 << op.la)) {
+#pragma unroll
+                        for (int k = 0; k < RB; ++k)
+                            if (k == op.la) {
+                                mm[0] = cmul(mm[0], dh[k][0]);
+                                mm[2] = cmul(mm[2], dh[k][0]);
+                                mm[1] = cmul(mm[1], dh[k][1]);
+                                mm[3] = cmul(mm[3], dh[k][1]);
+                                dh[k][0] = dh[k][1] = make_float2(1.f, 0.f);
+                            }
+                        dmask &= ~(1 << op.la);
+                        dpend = dmask != 0;
+                    }
+                    g1_dispatch<S, E, RB>(op.la, x, mm);
                 } else if (op.type == OP_D1) {
                     if (op.la < RB) {
                         dmul(op.la, m[0], m[3]);
@@ -455,8 +525,42 @@ __global__ void __launch_bounds__(kT >> RB, (S == 1 ? 2 : 1)) sweep_kernel(const
                         dpend = true;
                     }
                 } else if (op.type == OP_G2) {
-                    flush();
-                    g2_dispatch<S, E, RB>(op.la, op.lb, x, m);
+                    float2 mm[16];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) mm[e] = m[e];
+                    if (dpend) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) mm[e] = cmul(mm[e], dsc);
+                        dsc = make_float2(1.f, 0.f);
+                        dpend = dmask != 0;
+                    }
+                    const int both = (1 << op.la) | (1 << op.lb);
+                    if (dmask & both) {
+                        float2 fa[2] = {make_float2(1.f, 0.f), make_float2(1.f, 0.f)};
+                        float2 fb[2] = {fa[0], fa[1]};
+#pragma unroll
+                        for (int k = 0; k < RB; ++k) {
+                            if (k == op.la) {
+                                fa[0] = dh[k][0];
+                                fa[1] = dh[k][1];
+                                dh[k][0] = dh[k][1] = make_float2(1.f, 0.f);
+                            }
+                            if (k == op.lb) {
+                                fb[0] = dh[k][0];
+                                fb[1] = dh[k][1];
+                                dh[k][0] = dh[k][1] = make_float2(1.f, 0.f);
+                            }
+                        }
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float2 f = cmul(fa[c >> 1], fb[c & 1]);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) mm[4 * q + c] = cmul(mm[4 * q + c], f);
+                        }
+                        dmask &= ~both;
+                        dpend = dmask != 0;
+                    }
+                    g2_dispatch<S, E, RB>(op.la, op.lb, x, mm);
                 } else if (op.type == OP_SITE) {
                     flush();
                     site_dispatch<S, E, RB>(op.la, P, op, m, x, L, base, acc, lane, warp);
@@ -502,33 +606,45 @@ cudaError_t launch_t(int grid, const PassArgs& P, cudaStream_t st) {
 
 }  // namespace
 
-int sweep_reg_bits(int S) { return S == 1 ? 4 : 3; }
-
-int sweep_blocks_per_sm(int S, size_t smem) {
-    int nb = 0;
-    if (S == 1) {
-        cudaFuncSetAttribute(sweep_kernel<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<1, 4>, kT >> 4, smem);
-    } else if (S == 2) {
-        cudaFuncSetAttribute(sweep_kernel<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<2, 3>, kT >> 3, smem);
-    } else {
-        cudaFuncSetAttribute(sweep_kernel<3, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<3, 3>, kT >> 3, smem);
+// Register qubits per thread for an S-state launch.  Three states with four
+// register qubits need ~96 registers of amplitudes per thread (8 warps per
+// SM); with three register qubits the block has 512 threads (16 warps) but
+// a pass needs more phases.  NQS_SWEEP_RB (3 or 4) overrides the choice for
+// multi-state launches.
+int sweep_reg_bits(int S) {
+    static int forced = -1;
+    if (forced < 0) {
+        const char* e = getenv("NQS_SWEEP_RB");
+        forced = (e && (e[0] == '3' || e[0] == '4')) ? e[0] - '0' : 0;
     }
+    if (S == 1) return 4;
+    return forced ? forced : 3;
+}
+
+template <int S, int RB>
+int occupancy_t(size_t smem) {
+    int nb = 0;
+    cudaFuncSetAttribute(sweep_kernel<S, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<S, RB>, kT >> RB, smem);
     return nb > 0 ? nb : 1;
 }
 
-size_t sweep_smem_bytes(int S, int prog_words, int n_events) {
-    if (S == 1) return smem_for<1, 4>(prog_words, n_events);
-    if (S == 2) return smem_for<2, 3>(prog_words, n_events);
-    return smem_for<3, 3>(prog_words, n_events);
+int sweep_blocks_per_sm(int S, int RB, size_t smem) {
+    if (S == 1) return occupancy_t<1, 4>(smem);
+    if (S == 2) return RB == 4 ? occupancy_t<2, 4>(smem) : occupancy_t<2, 3>(smem);
+    return RB == 4 ? occupancy_t<3, 4>(smem) : occupancy_t<3, 3>(smem);
 }
 
-cudaError_t launch_sweep(int S, int grid, const PassArgs& P, cudaStream_t st) {
+size_t sweep_smem_bytes(int S, int RB, int prog_words, int n_events) {
+    if (S == 1) return smem_for<1, 4>(prog_words, n_events);
+    if (S == 2) return RB == 4 ? smem_for<2, 4>(prog_words, n_events) : smem_for<2, 3>(prog_words, n_events);
+    return RB == 4 ? smem_for<3, 4>(prog_words, n_events) : smem_for<3, 3>(prog_words, n_events);
+}
+
+cudaError_t launch_sweep(int S, int RB, int grid, const PassArgs& P, cudaStream_t st) {
     if (S == 1) return launch_t<1, 4>(grid, P, st);
-    if (S == 2) return launch_t<2, 3>(grid, P, st);
-    return launch_t<3, 3>(grid, P, st);
+    if (S == 2) return RB == 4 ? launch_t<2, 4>(grid, P, st) : launch_t<2, 3>(grid, P, st);
+    return RB == 4 ? launch_t<3, 4>(grid, P, st) : launch_t<3, 3>(grid, P, st);
 }
 
 }  // namespace nqs

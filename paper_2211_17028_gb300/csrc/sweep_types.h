@@ -106,9 +106,9 @@ int tile_pass_blocks_per_sm(int S, size_t smem);
 cudaError_t launch_tile_pass(int S, int grid, size_t smem, const PassArgs& P, cudaStream_t st);
 // register-resident kernel with TMA prefetch (tile width exactly 12 qubits)
 int sweep_reg_bits(int S);
-int sweep_blocks_per_sm(int S, size_t smem);
-size_t sweep_smem_bytes(int S, int prog_words, int n_events);
-cudaError_t launch_sweep(int S, int grid, const PassArgs& P, cudaStream_t st);
+int sweep_blocks_per_sm(int S, int RB, size_t smem);
+size_t sweep_smem_bytes(int S, int RB, int prog_words, int n_events);
+cudaError_t launch_sweep(int S, int RB, int grid, const PassArgs& P, cudaStream_t st);
 // reductions, finishers, fills
 cudaError_t launch_reduce2x2(const float2* phi, const float2* chi, int n, int q, double* partials, int grid,
                              cudaStream_t st);
