@@ -49,7 +49,8 @@ enum {
     NQS_ERR_CUDA = 6,           /* a CUDA runtime call or kernel launch failed */
     NQS_ERR_ORDER = 7,          /* call sequence violated (e.g. fidelity before prepare) */
     NQS_ERR_DEVICE_TIMEOUT = 8, /* a bounded device-side wait gave up (reported in result.status) */
-    NQS_ERR_UNSUPPORTED = 9     /* request outside the supported range (documented per call) */
+    NQS_ERR_UNSUPPORTED = 9,    /* request outside the supported range (documented per call) */
+    NQS_ERR_TOO_LARGE = 10      /* request exceeds a fixed capacity (nqs_reduced_matrix_noalloc) */
 };
 
 typedef struct nqs_circuit* nqs_handle;
@@ -202,6 +203,34 @@ int nqs_get_kernel_stats(nqs_handle h, int kind, nqs_kernel_stats* out);
 int nqs_reduced_matrix(const void* phi, const void* chi, int n, int qubit, double* R_out,
                        void* scratch, size_t scratch_bytes, void* stream);
 size_t nqs_reduced_matrix_scratch_bytes(int n);
+
+/* Allocation-free variant of nqs_reduced_matrix (the paper has no
+ * counterpart: this serves callers that cannot allocate device memory --
+ * hosts whose device heap is owned by another runtime's pool, latency-bound
+ * loops that cannot afford cudaMalloc's implicit device synchronisation,
+ * plugin environments that forbid dynamic device allocation).
+ *
+ * Same result as nqs_reduced_matrix: R_out (8 doubles: re, im of R00, R01,
+ * R10, R11) receives the reduced 2x2 matrix of phi and chi on `qubit`.  The
+ * per-block partial sums live in one fixed device array of
+ * NQS_NOALLOC_MAX_BLOCKS * 8 doubles (64 KiB) compiled into the library;
+ * every GPU that loads the library holds it until the process exits.  The
+ * call allocates nothing: no cudaMalloc, no cudaFree, no allocator callback.
+ *   - phi, chi: device, 2^n complex64 each, 16-byte aligned; n in 1..NQS_NOALLOC_MAX_QUBITS.
+ *   - R_out: device-accessible memory (device, managed or pinned host),
+ *     8-byte aligned; written by a kernel in `stream`.  Pageable host
+ *     memory is rejected with NQS_ERR_ARG.
+ *   - The first call on each device resolves the array's device address
+ *     (cudaGetSymbolAddress) with that device current and caches it.
+ *   - Every call on a device shares the one array and overwrites the
+ *     slots it reads, so sequential calls need no clearing; calls whose
+ *     kernels overlap on the GPU (different streams, no ordering between
+ *     them) race on the array and must be serialised by the caller.
+ * Errors: NQS_ERR_ARG (NULL, misaligned, qubit >= n, pageable R_out),
+ * NQS_ERR_TOO_LARGE (n > NQS_NOALLOC_MAX_QUBITS), NQS_ERR_CUDA. */
+#define NQS_NOALLOC_MAX_BLOCKS 1024
+#define NQS_NOALLOC_MAX_QUBITS 34
+int nqs_reduced_matrix_noalloc(const void* phi, const void* chi, int n, int qubit, double* R_out, void* stream);
 
 void nqs_destroy(nqs_handle h);
 const char* nqs_strerror(int code);

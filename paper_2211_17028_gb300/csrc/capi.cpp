@@ -307,6 +307,7 @@ const char* nqs_strerror(int code) {
         case NQS_ERR_ORDER: return "call order violated (prepare the noise first)";
         case NQS_ERR_DEVICE_TIMEOUT: return "a bounded device-side wait gave up";
         case NQS_ERR_UNSUPPORTED: return "request outside the supported range";
+        case NQS_ERR_TOO_LARGE: return "request exceeds the fixed scratch capacity of the allocation-free entry point";
         default: return "unknown status";
     }
 }

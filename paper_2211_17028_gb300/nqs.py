@@ -23,6 +23,8 @@ NQS_ERR_CUDA = 6
 NQS_ERR_ORDER = 7
 NQS_ERR_DEVICE_TIMEOUT = 8
 NQS_ERR_UNSUPPORTED = 9
+NQS_ERR_TOO_LARGE = 10
+NQS_NOALLOC_MAX_QUBITS = 34
 
 NQS_STATE_BASIS = 0
 NQS_STATE_DENSE = 1
@@ -99,6 +101,8 @@ _SIGS = {
     "nqs_reduced_matrix": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "nqs_reduced_matrix_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int]),
+    "nqs_reduced_matrix_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_void_p, ctypes.c_void_p]),
     "nqs_destroy": (None, [ctypes.c_void_p]),
     "nqs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "nqs_version": (ctypes.c_char_p, []),
@@ -308,6 +312,16 @@ def nqs_reduced_matrix(phi, chi, n, qubit, r_out, scratch, scratch_bytes, stream
     _check(_lib().nqs_reduced_matrix(ctypes.c_void_p(ptr(phi)), ctypes.c_void_p(ptr(chi)), n, qubit,
                                      ctypes.c_void_p(ptr(r_out)), ctypes.c_void_p(ptr(scratch)),
                                      scratch_bytes, _stream_ptr(stream)), "nqs_reduced_matrix")
+
+
+def nqs_reduced_matrix_noalloc(phi, chi, n, qubit, r_out, stream=None):
+    """Allocation-free reduced matrix: phi, chi, r_out are device pointers
+    (ints) or tensors; r_out must be device-accessible (8 doubles)."""
+    def ptr(x):
+        return x if isinstance(x, int) else x.data_ptr()
+    _check(_lib().nqs_reduced_matrix_noalloc(ctypes.c_void_p(ptr(phi)), ctypes.c_void_p(ptr(chi)), n, qubit,
+                                             ctypes.c_void_p(ptr(r_out)), _stream_ptr(stream)),
+           "nqs_reduced_matrix_noalloc")
 
 
 def nqs_reduced_matrix_scratch_bytes(n):
