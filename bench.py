@@ -278,18 +278,23 @@ def run_nqs(args):
     sweep = nqs.nqs_get_kernel_stats(h, 0)
     other = nqs.nqs_get_kernel_stats(h, 1)
     fills = nqs.nqs_get_kernel_stats(h, 2)
+    multi = nqs.nqs_get_kernel_stats(h, 3)    # branch-group passes (several states)
+    single = nqs.nqs_get_kernel_stats(h, 4)   # single-state passes
+    dom, dom_name = (multi, "sweep_kernel, 3-state branch-group passes") if multi["total_ms"] >= single["total_ms"] \
+        else (single, "sweep_kernel, single-state passes")
     nqs.nqs_set_profiling(h, 0)
     t_max, units = aggregate(elapsed, args.steps * n_terms, torch.device("cuda", dev))
     value = units / t_max
     res = slot(args.warmup + args.steps - 1).to_dict()
 
     peak, peak_src = measured_peaks()
-    achieved = sweep["algorithmic_bytes"] / (sweep["total_ms"] / 1000.0) / 1e9 if sweep["total_ms"] else 0.0
+    achieved = dom["algorithmic_bytes"] / (dom["total_ms"] / 1000.0) / 1e9 if dom["total_ms"] else 0.0
     traffic = None
     try:
-        with open(os.path.join(ROOT, "profiles", "pass_kernel_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", "sweep_traffic.json")) as f:
             tr = json.load(f)
-        if tr.get("workload") == args.workload and tr.get("kernel_source_sha") == kernel_source_sha():
+        if (tr.get("workload") == args.workload and tr.get("kernel_source_sha") == kernel_source_sha()
+                and tr.get("kernel") == ("multi" if dom is multi else "single")):
             traffic = tr.get("dram_bytes_per_launch")
     except Exception:
         pass
@@ -335,9 +340,12 @@ def run_nqs(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if peak else None, "traffic": traffic,
-                         "kernel": "pass_kernel (tile sweep passes)", "peak_source": peak_src,
-                         "launches": sweep["launches"], "ms": sweep["total_ms"],
-                         "share_of_step": sweep["total_ms"] / (1000.0 * elapsed) if elapsed else None},
+                         "kernel": dom_name, "peak_source": peak_src,
+                         "launches": dom["launches"], "ms": dom["total_ms"],
+                         "algorithmic_bytes_per_launch": dom["algorithmic_bytes"] / max(1, dom["launches"]),
+                         "share_of_step": dom["total_ms"] / (1000.0 * elapsed) if elapsed else None,
+                         "all_sweeps_gbs": sweep["algorithmic_bytes"] / (sweep["total_ms"] / 1000.0) / 1e9
+                         if sweep["total_ms"] else None},
             "gpu_launches": int(sweep["launches"] + other["launches"] + fills["launches"]),
             "clocks": clk,
             "e2e": e2e,
@@ -354,7 +362,7 @@ def run_nqs(args):
 
 def kernel_source_sha():
     import hashlib
-    p = os.path.join(ROOT, "paper_2211_17028_gb300", "csrc", "engine.cu")
+    p = os.path.join(ROOT, "paper_2211_17028_gb300", "csrc", "kernels_sweep.cu")
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 

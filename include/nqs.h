@@ -179,7 +179,9 @@ int nqs_get_info(nqs_handle h, nqs_info* out);
 
 /* Per-kernel timing of the calls made since profiling was switched on:
  * CUDA events recorded around every sweep-pass launch on the call's stream.
- * kind 0 = gate-sweep passes, 1 = finishers/reductions, 2 = other. */
+ * kind 0 = all gate-sweep passes, 1 = finishers/reductions, 2 = state fills,
+ * 3 = sweep passes over several states (branch groups), 4 = single-state
+ * sweep passes (kinds 3 and 4 split kind 0). */
 typedef struct {
     uint64_t launches;
     double total_ms;

@@ -267,7 +267,7 @@ int nqs_set_profiling(nqs_handle hh, int on) {
 
 int nqs_get_kernel_stats(nqs_handle hh, int kind, nqs_kernel_stats* out) {
     Handle* h = reinterpret_cast<Handle*>(hh);
-    if (!h || !out || kind < 0 || kind > 2) return NQS_ERR_ARG;
+    if (!h || !out || kind < 0 || kind > 4) return NQS_ERR_ARG;
     if (h->profiling) {
         int rc = engine_collect_stats(*h);
         if (rc) return rc;

@@ -103,7 +103,11 @@ struct Engine {
     int* err_dev = nullptr;
     // profiling
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
-    std::vector<std::pair<int, double>> ev_used;    // kind, bytes per used pair
+    struct EvUse {
+        int kind, sub;   // stats slot; second slot for sweep passes (3: several states, 4: one), -1 none
+        double bytes;
+    };
+    std::vector<EvUse> ev_used;
     size_t ev_next = 0;
     cudaStream_t last_stream = nullptr;
     bool has_result = false;
@@ -864,7 +868,7 @@ static int run_schedule(Handle& h, Engine& E, cudaStream_t st) {
             }
             e0 = E.ev_pool[E.ev_next].first;
             e1 = E.ev_pool[E.ev_next].second;
-            E.ev_used.push_back({kind, l.bytes});
+            E.ev_used.push_back({kind, l.kind == L_PASS ? (l.S > 1 ? 3 : 4) : -1, l.bytes});
             ++E.ev_next;
             cudaEventRecord(e0, st);
         }
@@ -894,6 +898,23 @@ static int run_schedule(Handle& h, Engine& E, cudaStream_t st) {
     return rc;
 }
 
+// Add the event timings of finished launches to the handle's statistics.
+static void fold_timings(Handle& h, Engine& E) {
+    for (size_t i = 0; i < E.ev_used.size(); ++i) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, E.ev_pool[i].first, E.ev_pool[i].second);
+        for (int slot : {E.ev_used[i].kind, E.ev_used[i].sub}) {
+            if (slot < 0) continue;
+            nqs_kernel_stats& s = h.stats[slot];
+            s.launches += 1;
+            s.total_ms += ms;
+            s.algorithmic_bytes += E.ev_used[i].bytes;
+        }
+    }
+    E.ev_used.clear();
+    E.ev_next = 0;
+}
+
 int engine_fidelity(Handle& h, const nqs_state* psi, const nqs_state* v, int level, nqs_result* out, void* stream) {
     if (!h.eng) h.eng = new Engine();
     Engine& E = *h.eng;
@@ -905,16 +926,7 @@ int engine_fidelity(Handle& h, const nqs_state* psi, const nqs_state* v, int lev
     if (h.profiling) {
         // fold finished timings of earlier calls before reusing the event pool
         cudaStreamSynchronize(E.last_stream);
-        for (size_t i = 0; i < E.ev_used.size(); ++i) {
-            float ms = 0;
-            cudaEventElapsedTime(&ms, E.ev_pool[i].first, E.ev_pool[i].second);
-            nqs_kernel_stats& s = h.stats[E.ev_used[i].first];
-            s.launches += 1;
-            s.total_ms += ms;
-            s.algorithmic_bytes += E.ev_used[i].second;
-        }
-        E.ev_used.clear();
-        E.ev_next = 0;
+        fold_timings(h, E);
     }
     rc = run_schedule(h, E, st);
     if (rc) return rc;
@@ -928,16 +940,7 @@ int engine_collect_stats(Handle& h) {
     if (!h.eng) return NQS_OK;
     Engine& E = *h.eng;
     if (cudaStreamSynchronize(E.last_stream) != cudaSuccess) return NQS_ERR_CUDA;
-    for (size_t i = 0; i < E.ev_used.size(); ++i) {
-        float ms = 0;
-        cudaEventElapsedTime(&ms, E.ev_pool[i].first, E.ev_pool[i].second);
-        nqs_kernel_stats& s = h.stats[E.ev_used[i].first];
-        s.launches += 1;
-        s.total_ms += ms;
-        s.algorithmic_bytes += E.ev_used[i].second;
-    }
-    E.ev_used.clear();
-    E.ev_next = 0;
+    fold_timings(h, E);
     return NQS_OK;
 }
 

@@ -108,7 +108,7 @@ struct Handle {
     Plan plan;
     Engine* eng = nullptr;
     bool profiling = false;
-    nqs_kernel_stats stats[3] = {};
+    nqs_kernel_stats stats[5] = {};
 };
 
 // engine entry points (engine.cu)
