@@ -45,6 +45,8 @@ WORKLOADS = {
     # small profiling case: same structure as the 30-qubit workload, 128 MiB states
     "qaoa24_l1": ("qaoa24", 1, "QAOA MaxCut n=24 (3-regular, p=4), 20 depolarizing, v=U|psi>, level 1"),
     "qaoa24_l2": ("qaoa24", 2, "QAOA MaxCut n=24 (3-regular, p=4), 20 depolarizing, v=U|psi>, level 2"),
+    "batch512": ("c4_batch", None, "512 circuits: width U{12..24}, depth U{10..30}, grid or line U3+CZ, "
+                 "5-40 mixed AD/PD/depolarizing noises (rates 1e-4..1e-2), level U{1,2}, v=U|psi>"),
 }
 
 
@@ -366,10 +368,81 @@ def kernel_source_sha():
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
+def run_batch(args):
+    """Batched evaluation of the 512-circuit set against the plain path: every
+    handle is warmed first (schedule built, workspace held), the plain path is
+    one nqs_fidelity per circuit, the batched path nqs_batch_fidelity (first
+    call captures the CUDA graph, then timed replays)."""
+    import math
+    import torch
+    import workloads as W
+    from paper_2211_17028_gb300 import nqs
+
+    torch.cuda.set_device(0)
+    nqs.use_torch_allocator()
+    ws = W.c4_batch(512)
+    circs, n_terms = [], 0
+    psis, vs, levels = [], [], []
+    stream = torch.cuda.current_stream()
+    for w in ws:
+        c = nqs.NoisyCircuit(W.to_ir_text(w))
+        circs.append(c)
+        psis.append(nqs.basis(0))
+        vs.append(nqs.ideal())
+        levels.append(w.levels[0])
+        n_terms += sum(math.comb(w.n_noise, u) * 3 ** u for u in range(w.levels[0] + 1))
+    hs = [c.h for c in circs]
+    # warm every handle: schedules and workspaces
+    for c, p, v, l in zip(circs, psis, vs, levels):
+        nqs.nqs_fidelity(c.h, p, v, l, stream)
+    torch.cuda.synchronize()
+    # plain path
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plain = []
+    rsz = ctypes.sizeof(nqs.nqs_result)
+    pinned = torch.empty(len(hs) * rsz, dtype=torch.uint8, pin_memory=True)
+    for i, (c, p, v, l) in enumerate(zip(circs, psis, vs, levels)):
+        nqs.nqs_fidelity(c.h, p, v, l, stream, out=nqs.nqs_result.from_address(pinned.data_ptr() + i * rsz))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) / 1000.0
+    plain = [nqs.nqs_result.from_address(pinned.data_ptr() + i * rsz).F for i in range(len(hs))]
+    # batched path: capture, then timed replays
+    outs = nqs.nqs_batch_fidelity(hs, psis, vs, levels, stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        outs = nqs.nqs_batch_fidelity(hs, psis, vs, levels, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_batch = e0.elapsed_time(e1) / 1000.0 / args.steps
+    dmax = max(abs(o.F - p) for o, p in zip(outs, plain))
+    line = {"metric": METRIC, "value": n_terms / t_batch, "unit": "terms/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": 2, "ms_per_step": 1000.0 * t_batch, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "batch512", "description": WORKLOADS["batch512"][2], "circuits": len(hs),
+                       "terms": n_terms, "l2": "mixed: states of 32 KiB .. 128 MiB"},
+            "plain": {"value": n_terms / t_plain, "ms": 1000.0 * t_plain},
+            "speedup_vs_plain": t_plain / t_batch, "max_abs_dF_vs_plain": dmax,
+            "time_to_dF_1e-6": {"batched_ms": 1000.0 * t_batch if dmax <= 1e-6 else None,
+                                "plain_ms": 1000.0 * t_plain},
+            "clocks": clk}
+    print(json.dumps(line))
+    for c in circs:
+        c.close()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch512":
+        return run_batch(args)
     return run_nqs(args)
 
 

@@ -134,9 +134,15 @@ int nqs_prepare_noise(nqs_handle h, const nqs_noise* sites, size_t n_sites, uint
 int nqs_fidelity(nqs_handle h, const nqs_state* psi, const nqs_state* v, int level,
                  nqs_result* out, void* stream);
 
-/* Evaluate `count` handles; entry k uses psis[k], vs[k], levels[k] and writes
- * outs[k].  Same semantics and errors as nqs_fidelity per entry; the first
- * failing entry's code is returned. */
+/* Evaluate `count` distinct handles; entry k uses psis[k], vs[k], levels[k]
+ * and writes outs[k] (same results as nqs_fidelity per entry).  The batch runs
+ * in rounds: round r executes the r-th launch of every circuit's schedule,
+ * one multi-circuit launch per launch kind, so narrow circuits share the GPU.
+ * Circuits are packed into waves whose buffers fit in free device memory;
+ * a batch that fits in one wave is captured as a CUDA graph and replayed by
+ * later calls with the same handles, states and levels (the handles keep
+ * their workspaces).  Errors as nqs_fidelity, checked for every entry before
+ * anything runs; NQS_ERR_ARG also for a handle listed twice. */
 int nqs_batch_fidelity(const nqs_handle* hs, size_t count, const nqs_state* psis,
                        const nqs_state* vs, const int* levels, nqs_result* outs, void* stream);
 

@@ -101,6 +101,7 @@ int nqs_prepare_noise(nqs_handle hh, const nqs_noise* sites, size_t n_sites, uin
         int rc = factor_noise(ns[i], (flags & NQS_PREP_PRUNE_ZERO_RANK) != 0, fac[i]);
         if (rc != NQS_OK) return rc;
     }
+    engine_batch_forget(h);
     engine_destroy(*h);
     h->circ.noises = ns;
     h->factors = fac;
@@ -141,11 +142,21 @@ int nqs_batch_fidelity(const nqs_handle* hs, size_t count, const nqs_state* psis
                        const int* levels, nqs_result* outs, void* stream) {
     if (count == 0) return NQS_OK;
     if (!hs || !psis || !vs || !levels || !outs) return NQS_ERR_ARG;
+    std::vector<Handle*> H(count);
     for (size_t i = 0; i < count; ++i) {
-        int rc = nqs_fidelity(hs[i], &psis[i], &vs[i], levels[i], &outs[i], stream);
-        if (rc != NQS_OK) return rc;
+        Handle* h = reinterpret_cast<Handle*>(hs[i]);
+        if (!h || levels[i] < 0) return NQS_ERR_ARG;
+        if (!h->prepared) return NQS_ERR_ORDER;
+        int rc = check_state(*h, &psis[i], false);
+        if (rc) return rc;
+        rc = check_state(*h, &vs[i], true);
+        if (rc) return rc;
+        if (std::min(levels[i], (int)h->factors.size()) > NQS_MAX_LEVEL) return NQS_ERR_ARG;
+        for (size_t j = 0; j < i; ++j)
+            if (H[j] == h) return NQS_ERR_ARG;   // each handle once per batch
+        H[i] = h;
     }
-    return NQS_OK;
+    return engine_batch_fidelity(H.data(), count, psis, vs, levels, outs, stream);
 }
 
 int nqs_enumerate_terms(nqs_handle hh, int level, uint64_t* rec, size_t cap, size_t* count) {
@@ -291,6 +302,7 @@ size_t nqs_reduced_matrix_scratch_bytes(int n) {
 void nqs_destroy(nqs_handle hh) {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h) return;
+    engine_batch_forget(h);
     engine_destroy(*h);
     delete h;
 }

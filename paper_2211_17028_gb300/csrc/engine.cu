@@ -30,89 +30,9 @@
 #include <map>
 #include <vector>
 
-#include "nqs_internal.h"
-#include "sweep_types.h"
+#include "engine_internal.h"
 
 namespace nqs {
-
-// ------------------------------------------------------------------ host side
-namespace {
-
-struct RunPass {
-    int op_off = 0, n_ops = 0;       // in the device op buffer
-    int k = 0, c = 0;
-    int local[kMaxTileQ] = {};
-    int nonlocal[kMaxQ] = {};
-    std::vector<int> lin;            // linear op index of each device op
-    std::vector<int> ev_site;        // site of reduction event e
-    int spawn_site = -1;             // site that spawns in this pass (at most one)
-    int phase_off = 0, n_phases = 0; // register-resident phases (device phase buffer)
-};
-
-struct Run {
-    std::vector<RunPass> passes;     // in execution order
-};
-
-enum LaunchKind { L_PASS, L_FINISH, L_FILL, L_COPY, L_REDUCE2, L_SUM };
-
-struct Launch {
-    LaunchKind kind;
-    int S = 1;
-    PassArgs args{};
-    int op_index = 0;                // offset of the first device op (rebased onto the device table)
-    int prog_index = 0;              // offset (16-byte words) of the launch's program
-    bool rt = false;                 // register-resident kernel
-    int rb = 4;                      // its register qubits
-    int grid = 0;
-    size_t smem = 0;
-    // finisher
-    int n_red = 0, fin_grid = 0;
-    size_t desc_off = 0;
-    // fill / copy
-    float2* dst = nullptr;
-    const float2* src = nullptr;
-    unsigned long long bits = 0;
-    double bytes = 0;                // algorithmic bytes (pass kernels)
-};
-
-}  // namespace
-
-struct Engine {
-    int sm_count = 0;
-    int device = -1;
-    // persistent device buffers
-    void* buf = nullptr;             // one allocation for states
-    size_t buf_bytes = 0;
-    void* aux = nullptr;             // ops, mats, tables, partials, term values, result
-    size_t aux_bytes = 0;
-    // schedule cache key
-    int level = -1, psi_kind = -1, v_kind = -1;
-    unsigned long long psi_bits = 0, v_bits = 0;
-    const void* psi_dev = nullptr;
-    const void* v_dev = nullptr;
-    std::vector<Launch> launches;
-    double bound = 0;
-    long long n_terms = 0;
-    int eff_level = 0;
-    long long* level_off_dev = nullptr;
-    double* term_vals = nullptr;
-    nqs_result* res_dev = nullptr;
-    FinishDesc* desc_dev = nullptr;
-    double* partials = nullptr;
-    double* kmats_dev = nullptr;
-    int* err_dev = nullptr;
-    // profiling
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
-    struct EvUse {
-        int kind, sub;   // stats slot; second slot for sweep passes (3: several states, 4: one), -1 none
-        double bytes;
-    };
-    std::vector<EvUse> ev_used;
-    size_t ev_next = 0;
-    cudaStream_t last_stream = nullptr;
-    bool has_result = false;
-    uint64_t upload_bytes = 0;
-};
 
 namespace {
 
@@ -363,6 +283,7 @@ struct Builder {
     Tables tab;
     std::vector<DevOp> dops;
     std::vector<uint4> prog;          // programs of the register-resident launches
+    bool too_big = false;             // a launch would not fit in shared memory
     bool rt = false;                  // register-resident kernel (tile of exactly 12 qubits)
     std::vector<FinishDesc> descs;
     std::vector<Launch> L;
@@ -425,6 +346,8 @@ struct Builder {
             l.args.ops_word = pi.ops_word;
             l.args.mats_word = pi.mats_word;
             l.args.n_phases = pi.n_phases;
+            // static shared memory of the kernel stays below 4 KiB
+            if (sweep_smem_bytes(S, l.rb, pi.n_words, l.args.n_events) + 4096 > E.smem_optin) too_big = true;
         }
         for (int s = 0; s < S; ++s) {
             l.args.in[s] = in[s];
@@ -548,7 +471,7 @@ struct Builder {
 
 }  // namespace
 
-static int engine_init(Engine& E) {
+int engine_init(Engine& E) {
     if (E.device >= 0) return NQS_OK;
     int dev;
     if (cudaGetDevice(&dev) != cudaSuccess) return NQS_ERR_CUDA;
@@ -556,10 +479,11 @@ static int engine_init(Engine& E) {
     if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return NQS_ERR_CUDA;
     E.device = dev;
     E.sm_count = prop.multiProcessorCount;
+    E.smem_optin = prop.sharedMemPerBlockOptin;
     return NQS_OK;
 }
 
-static void engine_release(Engine& E, void* stream) {
+void engine_release(Engine& E, void* stream) {
     if (E.buf) dev_free(E.buf, E.buf_bytes, stream);
     if (E.aux) dev_free(E.aux, E.aux_bytes, stream);
     E.buf = E.aux = nullptr;
@@ -569,7 +493,7 @@ static void engine_release(Engine& E, void* stream) {
 }
 
 // Build (or reuse) the schedule for this level and state kinds.
-static int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* v, int level,
+int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* v, int level,
                           void* stream) {
     const Plan& plan = h.plan;
     const int N = (int)h.factors.size();
@@ -577,6 +501,7 @@ static int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_
         E.v_bits == v->bits && E.psi_dev == psi->dev && E.v_dev == v->dev)
         return NQS_OK;
     engine_release(E, stream);
+    ++E.gen;
 
     Builder B(h, E, level);
     std::vector<int> m(N);
@@ -750,6 +675,10 @@ static int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_
         l.kind = L_SUM;
         B.L.push_back(l);
     }
+    if (B.too_big) {
+        engine_release(E, stream);
+        return NQS_ERR_UNSUPPORTED;
+    }
 
     // --- aux allocation: ops, mats, ckpt table, kmats, descs, partials, term values, level offsets, result
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -844,16 +773,33 @@ static int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_
     return NQS_OK;
 }
 
-static int launch_pass(const Launch& l, cudaStream_t st) {
+int launch_pass(const Launch& l, cudaStream_t st) {
     if (l.rt) return cuda_err(launch_sweep(l.S, l.rb, l.grid, l.args, st));
     return cuda_err(launch_tile_pass(l.S, l.grid, l.smem, l.args, st));
 }
 
-static int run_schedule(Handle& h, Engine& E, cudaStream_t st) {
+// One launch of a schedule on stream `st`.
+int run_launch(Handle& h, Engine& E, const Launch& l, cudaStream_t st) {
     const long long dim = 1ll << h.plan.n;
-    int rc = NQS_OK;
-    int fill_grid = (int)std::max<long long>(1, std::min<long long>(E.sm_count * 8, dim / 512));
-    rc = cuda_err(cudaMemsetAsync(E.err_dev, 0, sizeof(int), st));
+    const int fill_grid = (int)std::max<long long>(1, std::min<long long>(E.sm_count * 8, dim / 512));
+    switch (l.kind) {
+        case L_PASS: return launch_pass(l, st);
+        case L_FINISH:
+            return cuda_err(
+                launch_finish(E.partials, l.fin_grid, E.desc_dev + l.desc_off, E.kmats_dev, E.term_vals, l.n_red, st));
+        case L_FILL: return cuda_err(launch_basis_fill(l.dst, dim, l.bits, fill_grid, st));
+        case L_COPY:
+            return cuda_err(cudaMemcpyAsync(l.dst, l.src, dim * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+        case L_REDUCE2: return cuda_err(launch_reduce2x2(l.src, l.dst, h.plan.n, 0, E.partials, l.grid, st));
+        case L_SUM:
+            return cuda_err(launch_level_sum(E.term_vals, E.level_off_dev, E.eff_level, E.res_dev, E.bound, E.n_terms,
+                                             E.err_dev, st));
+    }
+    return NQS_ERR_ARG;
+}
+
+int run_schedule(Handle& h, Engine& E, cudaStream_t st) {
+    int rc = cuda_err(cudaMemsetAsync(E.err_dev, 0, sizeof(int), st));
     if (rc != NQS_OK) return rc;
     for (const Launch& l : E.launches) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -872,26 +818,7 @@ static int run_schedule(Handle& h, Engine& E, cudaStream_t st) {
             ++E.ev_next;
             cudaEventRecord(e0, st);
         }
-        switch (l.kind) {
-            case L_PASS: rc = launch_pass(l, st); break;
-            case L_FINISH:
-                rc = cuda_err(launch_finish(E.partials, l.fin_grid, E.desc_dev + l.desc_off, E.kmats_dev,
-                                            E.term_vals, l.n_red, st));
-                break;
-            case L_FILL:
-                rc = cuda_err(launch_basis_fill(l.dst, dim, l.bits, fill_grid, st));
-                break;
-            case L_COPY:
-                rc = cuda_err(cudaMemcpyAsync(l.dst, l.src, dim * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-                break;
-            case L_REDUCE2:
-                rc = cuda_err(launch_reduce2x2(l.src, l.dst, h.plan.n, 0, E.partials, l.grid, st));
-                break;
-            case L_SUM:
-                rc = cuda_err(launch_level_sum(E.term_vals, E.level_off_dev, E.eff_level, E.res_dev, E.bound,
-                                               E.n_terms, E.err_dev, st));
-                break;
-        }
+        rc = run_launch(h, E, l, st);
         if (timed) cudaEventRecord(e1, st);
         if (rc != NQS_OK) return rc;
     }

@@ -1,0 +1,100 @@
+// Schedule and engine state shared by the single-circuit engine (engine.cu)
+// and the batch executor (batch.cu).  Internal to libnqs.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "nqs_internal.h"
+#include "sweep_types.h"
+
+namespace nqs {
+
+
+struct RunPass {
+    int op_off = 0, n_ops = 0;       // in the device op buffer
+    int k = 0, c = 0;
+    int local[kMaxTileQ] = {};
+    int nonlocal[kMaxQ] = {};
+    std::vector<int> lin;            // linear op index of each device op
+    std::vector<int> ev_site;        // site of reduction event e
+    int spawn_site = -1;             // site that spawns in this pass (at most one)
+    int phase_off = 0, n_phases = 0; // register-resident phases (device phase buffer)
+};
+
+struct Run {
+    std::vector<RunPass> passes;     // in execution order
+};
+
+enum LaunchKind { L_PASS, L_FINISH, L_FILL, L_COPY, L_REDUCE2, L_SUM };
+
+struct Launch {
+    LaunchKind kind;
+    int S = 1;
+    PassArgs args{};
+    int op_index = 0;                // offset of the first device op (rebased onto the device table)
+    int prog_index = 0;              // offset (16-byte words) of the launch's program
+    bool rt = false;                 // register-resident kernel
+    int rb = 4;                      // its register qubits
+    int grid = 0;
+    size_t smem = 0;
+    // finisher
+    int n_red = 0, fin_grid = 0;
+    size_t desc_off = 0;
+    // fill / copy
+    float2* dst = nullptr;
+    const float2* src = nullptr;
+    unsigned long long bits = 0;
+    double bytes = 0;                // algorithmic bytes (pass kernels)
+};
+
+struct Engine {
+    int sm_count = 0;
+    size_t smem_optin = 0;           // largest dynamic shared memory per block
+    int device = -1;
+    // persistent device buffers
+    void* buf = nullptr;             // one allocation for states
+    size_t buf_bytes = 0;
+    void* aux = nullptr;             // ops, mats, tables, partials, term values, result
+    size_t aux_bytes = 0;
+    // schedule cache key
+    int level = -1, psi_kind = -1, v_kind = -1;
+    unsigned long long psi_bits = 0, v_bits = 0;
+    const void* psi_dev = nullptr;
+    const void* v_dev = nullptr;
+    std::vector<Launch> launches;
+    double bound = 0;
+    long long n_terms = 0;
+    int eff_level = 0;
+    long long* level_off_dev = nullptr;
+    double* term_vals = nullptr;
+    nqs_result* res_dev = nullptr;
+    FinishDesc* desc_dev = nullptr;
+    double* partials = nullptr;
+    double* kmats_dev = nullptr;
+    int* err_dev = nullptr;
+    // profiling
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+    struct EvUse {
+        int kind, sub;   // stats slot; second slot for sweep passes (3: several states, 4: one), -1 none
+        double bytes;
+    };
+    std::vector<EvUse> ev_used;
+    size_t ev_next = 0;
+    cudaStream_t last_stream = nullptr;
+    bool has_result = false;
+    uint64_t upload_bytes = 0;
+    uint64_t gen = 0;                // bumped whenever the schedule is rebuilt
+};
+
+
+// schedule construction and execution (engine.cu)
+int engine_init(Engine& E);
+void engine_release(Engine& E, void* stream);
+int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* v, int level, void* stream);
+int run_schedule(Handle& h, Engine& E, cudaStream_t st);
+int run_launch(Handle& h, Engine& E, const Launch& l, cudaStream_t st);
+int launch_pass(const Launch& l, cudaStream_t st);
+
+}  // namespace nqs

@@ -169,11 +169,13 @@ void build_plan(const Circuit& c, const std::vector<Factors>& f, int tile_qubits
                 for (int cc = 0; cc < 4; ++cc)
                     if (r != cc) o.m[4 * r + cc] = cd(0);
     }
-    p.free_passes = segment(p, false, 8);
-    p.sitecut_passes = segment(p, true, 8);
+    // bounded passes: at most 4 reductions and 96 operations each, so a pass's
+    // program and reduction slots fit next to the tiles in shared memory
+    p.free_passes = segment(p, false, 4, 96);
+    p.sitecut_passes = segment(p, true, 4, 96);
 }
 
-std::vector<PassSpec> segment(const Plan& p, bool cut_after_sites, int max_sites_per_pass) {
+std::vector<PassSpec> segment(const Plan& p, bool cut_after_sites, int max_sites_per_pass, int max_ops_per_pass) {
     std::vector<PassSpec> out;
     const int nops = (int)p.ops.size();
     auto needs = [&](const HostOp& o, int q[2]) {
@@ -209,7 +211,7 @@ std::vector<PassSpec> segment(const Plan& p, bool cut_after_sites, int max_sites
             int extra = 0;
             for (int j = 0; j < cnt; ++j) extra += in[q[j]] ? 0 : 1;
             if (cnt == 2 && q[0] == q[1]) extra = in[q[0]] ? 0 : 1;
-            if (count + extra > p.k) break;
+            if (count + extra > p.k || i - ps.op_begin >= max_ops_per_pass) break;
             for (int j = 0; j < cnt; ++j)
                 if (!in[q[j]]) {
                     in[q[j]] = 1;

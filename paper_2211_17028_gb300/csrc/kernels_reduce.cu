@@ -70,15 +70,14 @@ __device__ void sum_partials(const double* part, int grid, double* R, double* sc
 
 // One block per reduction slot (event, state): R from the partials, then
 // X = |sum_ab K[a][b] R[a][b]|^2 for each factor of the slot.
-__global__ void __launch_bounds__(kThreads) finish_kernel(const double* __restrict__ partials, int grid,
-                                                          const FinishDesc* __restrict__ desc,
-                                                          const double* __restrict__ kmats,
-                                                          double* __restrict__ term_vals) {
+__device__ __forceinline__ void finish_slot(const double* __restrict__ partials, int grid, int slot,
+                                            const FinishDesc* __restrict__ desc, const double* __restrict__ kmats,
+                                            double* __restrict__ term_vals) {
     __shared__ double scratch[8 * kThreads];
     __shared__ double R[8];
-    sum_partials(partials + (size_t)blockIdx.x * grid * 8, grid, R, scratch);
+    sum_partials(partials + (size_t)slot * grid * 8, grid, R, scratch);
     if (threadIdx.x < 4) {
-        FinishDesc d = desc[blockIdx.x * 4 + threadIdx.x];
+        FinishDesc d = desc[slot * 4 + threadIdx.x];
         if (d.rank >= 0) {
             const double* K = kmats + d.kmat;
             double re = 0, im = 0;
@@ -92,6 +91,26 @@ __global__ void __launch_bounds__(kThreads) finish_kernel(const double* __restri
     }
 }
 
+__global__ void __launch_bounds__(kThreads) finish_kernel(const double* __restrict__ partials, int grid,
+                                                          const FinishDesc* __restrict__ desc,
+                                                          const double* __restrict__ kmats,
+                                                          double* __restrict__ term_vals) {
+    finish_slot(partials, grid, blockIdx.x, desc, kmats, term_vals);
+}
+
+// finishers of many circuits: unit u owns blocks [blk_begin[u], blk_begin[u+1])
+__global__ void __launch_bounds__(kThreads) finish_kernel_batched(const FinishUnit* __restrict__ units,
+                                                                  const int* __restrict__ blk_begin, int n_units) {
+    int lo = 0, hi = n_units;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (blk_begin[mid] <= (int)blockIdx.x) lo = mid;
+        else hi = mid;
+    }
+    const FinishUnit u = units[lo];
+    finish_slot(u.partials, u.grid, (int)blockIdx.x - blk_begin[lo], u.desc, u.kmats, u.vals);
+}
+
 // One block: fixed-order sum of per-block partials into 8 doubles.
 __global__ void __launch_bounds__(kThreads) partials_sum_kernel(const double* __restrict__ part, int grid,
                                                                 double* __restrict__ R) {
@@ -102,10 +121,11 @@ __global__ void __launch_bounds__(kThreads) partials_sum_kernel(const double* __
 }
 
 // Neumaier-compensated per-level sums in canonical order, one block.
-__global__ void __launch_bounds__(kThreads) level_sum_kernel(const double* __restrict__ vals,
+__device__ __forceinline__ void level_sum_body(const double* __restrict__ vals,
                                                              const long long* __restrict__ level_off, int level,
                                                              nqs_result* __restrict__ res, double bound,
-                                                             long long n_terms, const int* __restrict__ err) {
+                                                             long long n_terms, const int* __restrict__ err,
+                                               nqs_result* __restrict__ copy) {
     __shared__ double s_sum[kThreads], s_comp[kThreads];
     __shared__ double T[NQS_MAX_LEVEL + 1];
     const int tid = threadIdx.x;
@@ -155,6 +175,33 @@ __global__ void __launch_bounds__(kThreads) level_sum_kernel(const double* __res
         res->bound = bound;
         res->level = level;
         res->status = (err && *err) ? *err : NQS_OK;
+        if (copy) *copy = *res;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) level_sum_kernel(const double* __restrict__ vals,
+                                                             const long long* __restrict__ level_off, int level,
+                                                             nqs_result* __restrict__ res, double bound,
+                                                             long long n_terms, const int* __restrict__ err) {
+    level_sum_body(vals, level_off, level, res, bound, n_terms, err, nullptr);
+}
+
+// per-level sums of many circuits, one block each; results also gathered into one array
+__global__ void __launch_bounds__(kThreads) level_sum_kernel_batched(const SumUnit* __restrict__ units) {
+    const SumUnit u = units[blockIdx.x];
+    level_sum_body(u.vals, u.level_off, u.level, u.res, u.bound, u.n_terms, u.err, u.copy);
+}
+
+// basis-state fills of many circuits: blockIdx.y selects the unit
+__global__ void basis_fill_kernel_batched(const FillUnit* __restrict__ units) {
+    const FillUnit u = units[blockIdx.y];
+    long long stride = (long long)gridDim.x * blockDim.x;
+    float4* o4 = reinterpret_cast<float4*>(u.dst);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (u.dim >> 1); i += stride) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((unsigned long long)(2 * i) == u.bits) v.x = 1.f;
+        if ((unsigned long long)(2 * i + 1) == u.bits) v.z = 1.f;
+        o4[i] = v;
     }
 }
 
@@ -195,6 +242,22 @@ cudaError_t launch_level_sum(const double* vals, const long long* level_off, int
 
 cudaError_t launch_basis_fill(float2* out, long long dim, unsigned long long bits, int grid, cudaStream_t st) {
     basis_fill_kernel<<<grid, kThreads, 0, st>>>(out, dim, bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_batched(const FinishUnit* units, const int* blk_begin, int n_units, int total_blocks,
+                                  cudaStream_t st) {
+    finish_kernel_batched<<<total_blocks, kThreads, 0, st>>>(units, blk_begin, n_units);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level_sum_batched(const SumUnit* units, int n_units, cudaStream_t st) {
+    level_sum_kernel_batched<<<n_units, kThreads, 0, st>>>(units);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_batched(const FillUnit* units, int n_units, cudaStream_t st) {
+    basis_fill_kernel_batched<<<dim3(64, n_units), kThreads, 0, st>>>(units);
     return cudaGetLastError();
 }
 

@@ -58,6 +58,11 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
         : "memory");
 }
 
+// bulk prefetch of global memory into L2 (no shared-memory destination)
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -338,8 +343,11 @@ __device__ __forceinline__ void site_dispatch(int i, const PassArgs& P, const Op
     else if constexpr (RB > 3) site_reg<3>(P, op, m, x, L, base, acc, lane, warp);
 }
 
+// The tiles of one pass, processed by block `cta` of `nctas` (tiles cta,
+// cta + nctas, ...).  Shared by the single-pass kernel and the batched kernel
+// that runs the passes of many circuits in one launch.
 template <int S, int RB>
-__global__ void __launch_bounds__(kT >> RB, (S == 1 ? 2 : 1)) sweep_kernel(const PassArgs P) {
+__device__ __forceinline__ void sweep_body(const PassArgs& P, const int cta, const int nctas) {
     constexpr int E = 1 << RB;
     constexpr int NT = kT >> RB;
     constexpr int NW = NT / 32;
@@ -350,6 +358,8 @@ __global__ void __launch_bounds__(kT >> RB, (S == 1 ? 2 : 1)) sweep_kernel(const
     double* acc = reinterpret_cast<double*>(prog + P.prog_words);                   // [ev][S][NW][8]
     __shared__ __align__(8) uint64_t bar;
     __shared__ unsigned long long hi_off[kChunks];
+    __shared__ const float2* red_phi[kMaxEvents];   // phi of the pass's reductions, prefetched into L2
+    __shared__ int n_red;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < P.prog_words; i += NT) prog[i] = P.prog[i];
@@ -368,6 +378,13 @@ __global__ void __launch_bounds__(kT >> RB, (S == 1 ? 2 : 1)) sweep_kernel(const
     const DevPhase* phases = reinterpret_cast<const DevPhase*>(prog);
     const OpRec* ops = reinterpret_cast<const OpRec*>(prog + P.ops_word);
     const float2* mats = reinterpret_cast<const float2*>(prog + P.mats_word);
+    if (tid == 0) {
+        int c = 0;
+        for (int o = 0; o < P.n_ops && c < kMaxEvents; ++o)
+            if (ops[o].type == OP_SITE && (ops[o].flags & FL_REDUCE)) red_phi[c++] = P.ckpt[ops[o].site];
+        n_red = c;
+    }
+    __syncthreads();
 
     auto tile_base = [&](long long t) {
         unsigned long long b = 0;
@@ -378,25 +395,30 @@ __global__ void __launch_bounds__(kT >> RB, (S == 1 ? 2 : 1)) sweep_kernel(const
     // every thread issues its share of the copies (no warp arrives late at
     // the next barrier); the mbarrier phase cannot complete before thread 0's
     // arrive.expect_tx, whatever order the copies land in
-    auto prefetch = [&](long long t) {
-        const unsigned long long b = tile_base(t);
+    // the phi tiles the pass's reductions will read go to L2 at the same time
+    auto prefetch = [&](unsigned long long b) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (tid == 0) mbar_arrive_expect_tx(&bar, (uint32_t)(S * kT * sizeof(float2)));
         for (int q = tid; q < S * kChunks; q += NT) {
             const int s = q / kChunks, h = q % kChunks;
             bulk_copy_g2s(pf + s * kT + h * kChunk, P.in[s] + (b | hi_off[h]), kChunk * sizeof(float2), &bar);
         }
+        for (int q = tid; q < n_red * kChunks; q += NT) {
+            const int e = q / kChunks, h = q % kChunks;
+            bulk_prefetch_l2(red_phi[e] + (b | hi_off[h]), kChunk * sizeof(float2));
+        }
     };
 
-    long long t = blockIdx.x;
-    if (t < P.n_tiles) prefetch(t);
+    long long t = cta;
+    unsigned long long base_next = t < P.n_tiles ? tile_base(t) : 0ull;
+    if (t < P.n_tiles) prefetch(base_next);
     uint32_t parity = 0;
     bool failed = false;
     float2 x[S][E];
     Layout<RB> L;
 
-    for (; t < P.n_tiles; t += gridDim.x) {
-        const unsigned long long base = tile_base(t);
+    for (; t < P.n_tiles; t += nctas) {
+        const unsigned long long base = base_next;
         const bool ok = mbar_wait_bounded(&bar, parity);
         if (__syncthreads_or(!ok)) {
             failed = true;
@@ -409,7 +431,10 @@ __global__ void __launch_bounds__(kT >> RB, (S == 1 ? 2 : 1)) sweep_kernel(const
 #pragma unroll
             for (int r = 0; r < E; ++r) x[s][r] = pf[s * kT + (L.jT | jr_of(L, r))];
         __syncthreads();   // the staging buffer is free again
-        if (t + gridDim.x < P.n_tiles) prefetch(t + gridDim.x);
+        if (t + nctas < P.n_tiles) {
+            base_next = tile_base(t + nctas);
+            prefetch(base_next);
+        }
 
         // pending diagonal factor: scalar + per-register-qubit pairs
         float2 dsc = make_float2(1.f, 0.f);
@@ -569,10 +594,11 @@ __global__ void __launch_bounds__(kT >> RB, (S == 1 ? 2 : 1)) sweep_kernel(const
             flush();
         }
 
+        const unsigned long long gb = base | L.gT;
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
-            for (int r = 0; r < E; ++r) __stcs(P.out[s] + (base | L.gT | gr_of(L, r)), x[s][r]);
+            for (int r = 0; r < E; ++r) __stcs(P.out[s] + (gb | gr_of(L, r)), x[s][r]);
     }
 
     if (failed) {
@@ -585,8 +611,32 @@ __global__ void __launch_bounds__(kT >> RB, (S == 1 ? 2 : 1)) sweep_kernel(const
         const int e = i & 7, s = (i >> 3) % S, ev = (i >> 3) / S;
         double v = 0.0;
         for (int w = 0; w < NW; ++w) v += acc[((ev * S + s) * NW + w) * 8 + e];
-        P.partials[((size_t)(ev * S + s) * gridDim.x + blockIdx.x) * 8 + e] = v;
+        P.partials[((size_t)(ev * S + s) * nctas + cta) * 8 + e] = v;
     }
+}
+
+template <int S, int RB>
+__global__ void __launch_bounds__(kT >> RB, (S == 1 ? 2 : 1)) sweep_kernel(const PassArgs P) {
+    sweep_body<S, RB>(P, blockIdx.x, gridDim.x);
+}
+
+// Passes of many circuits in one launch: unit u owns blocks
+// [cta_begin[u], cta_begin[u+1]); its arguments are staged in shared memory.
+template <int S, int RB>
+__global__ void __launch_bounds__(kT >> RB, (S == 1 ? 2 : 1))
+    sweep_kernel_batched(const PassArgs* __restrict__ units, const int* __restrict__ cta_begin, int n_units) {
+    __shared__ __align__(16) PassArgs sP;
+    int lo = 0, hi = n_units;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (cta_begin[mid] <= (int)blockIdx.x) lo = mid;
+        else hi = mid;
+    }
+    const int* src = reinterpret_cast<const int*>(units + lo);
+    int* dst = reinterpret_cast<int*>(&sP);
+    for (int i = threadIdx.x; i < (int)(sizeof(PassArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    sweep_body<S, RB>(sP, (int)blockIdx.x - cta_begin[lo], cta_begin[lo + 1] - cta_begin[lo]);
 }
 
 template <int S, int RB>
@@ -611,6 +661,16 @@ cudaError_t launch_t(int grid, const PassArgs& P, cudaStream_t st) {
 // SM); with three register qubits the block has 512 threads (16 warps) but
 // a pass needs more phases.  NQS_SWEEP_RB (3 or 4) overrides the choice for
 // multi-state launches.
+template <int S, int RB>
+cudaError_t launch_batched_t(const PassArgs* units, const int* cta_begin, int n_units, int total_ctas, size_t smem,
+                             cudaStream_t st) {
+    cudaError_t e =
+        cudaFuncSetAttribute(sweep_kernel_batched<S, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    sweep_kernel_batched<S, RB><<<total_ctas, kT >> RB, smem, st>>>(units, cta_begin, n_units);
+    return cudaGetLastError();
+}
+
 int sweep_reg_bits(int S) {
     static int forced = -1;
     if (forced < 0) {
@@ -645,6 +705,16 @@ cudaError_t launch_sweep(int S, int RB, int grid, const PassArgs& P, cudaStream_
     if (S == 1) return launch_t<1, 4>(grid, P, st);
     if (S == 2) return RB == 4 ? launch_t<2, 4>(grid, P, st) : launch_t<2, 3>(grid, P, st);
     return RB == 4 ? launch_t<3, 4>(grid, P, st) : launch_t<3, 3>(grid, P, st);
+}
+
+cudaError_t launch_sweep_batched(int S, int RB, const PassArgs* units, const int* cta_begin, int n_units,
+                                 int total_ctas, size_t smem, cudaStream_t st) {
+    if (S == 1) return launch_batched_t<1, 4>(units, cta_begin, n_units, total_ctas, smem, st);
+    if (S == 2)
+        return RB == 4 ? launch_batched_t<2, 4>(units, cta_begin, n_units, total_ctas, smem, st)
+                       : launch_batched_t<2, 3>(units, cta_begin, n_units, total_ctas, smem, st);
+    return RB == 4 ? launch_batched_t<3, 4>(units, cta_begin, n_units, total_ctas, smem, st)
+                   : launch_batched_t<3, 3>(units, cta_begin, n_units, total_ctas, smem, st);
 }
 
 }  // namespace nqs

@@ -96,7 +96,7 @@ struct Plan {
 };
 
 void build_plan(const Circuit& c, const std::vector<Factors>& f, int tile_qubits, Plan& out);
-std::vector<PassSpec> segment(const Plan& p, bool cut_after_sites, int max_sites_per_pass);
+std::vector<PassSpec> segment(const Plan& p, bool cut_after_sites, int max_sites_per_pass, int max_ops_per_pass);
 
 // ------------------------------------------------------------------- handle
 struct Engine;   // device-side state (engine.cu)
@@ -115,6 +115,9 @@ struct Handle {
 int engine_fidelity(Handle& h, const nqs_state* psi, const nqs_state* v, int level,
                     nqs_result* out, void* stream);
 int engine_term_values(Handle& h, double* out, size_t cap, size_t* count);
+int engine_batch_fidelity(Handle** hs, size_t count, const nqs_state* psis, const nqs_state* vs, const int* levels,
+                          nqs_result* outs, void* stream);
+void engine_batch_forget(Handle* h);   // drop a cached batch plan that uses h
 void engine_destroy(Handle& h);
 uint64_t engine_workspace_bytes(const Handle& h);
 uint64_t engine_upload_bytes(const Handle& h);

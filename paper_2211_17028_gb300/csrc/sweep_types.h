@@ -89,6 +89,34 @@ struct FinishDesc {
     int pad;
 };
 
+// batched bookkeeping units (one per circuit of a batch round)
+struct FinishUnit {
+    const double* partials;
+    const FinishDesc* desc;
+    const double* kmats;
+    double* vals;
+    int grid;
+    int pad;
+};
+
+struct FillUnit {
+    float2* dst;
+    long long dim;
+    unsigned long long bits;
+};
+
+struct SumUnit {
+    const double* vals;
+    const long long* level_off;
+    nqs_result* res;
+    nqs_result* copy;    // gathered copy of the result (batch output array)
+    const int* err;
+    double bound;
+    long long n_terms;
+    int level;
+    int pad;
+};
+
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -109,6 +137,10 @@ int sweep_reg_bits(int S);
 int sweep_blocks_per_sm(int S, int RB, size_t smem);
 size_t sweep_smem_bytes(int S, int RB, int prog_words, int n_events);
 cudaError_t launch_sweep(int S, int RB, int grid, const PassArgs& P, cudaStream_t st);
+// the passes of many circuits in one launch: unit u runs on blocks
+// [cta_begin[u], cta_begin[u+1]) (device arrays); all units share S and RB
+cudaError_t launch_sweep_batched(int S, int RB, const PassArgs* units, const int* cta_begin, int n_units,
+                                 int total_ctas, size_t smem, cudaStream_t st);
 // reductions, finishers, fills
 cudaError_t launch_reduce2x2(const float2* phi, const float2* chi, int n, int q, double* partials, int grid,
                              cudaStream_t st);
@@ -118,5 +150,9 @@ cudaError_t launch_partials_sum(const double* part, int grid, double* R, cudaStr
 cudaError_t launch_level_sum(const double* vals, const long long* level_off, int level, nqs_result* res,
                              double bound, long long n_terms, const int* err, cudaStream_t st);
 cudaError_t launch_basis_fill(float2* out, long long dim, unsigned long long bits, int grid, cudaStream_t st);
+cudaError_t launch_finish_batched(const FinishUnit* units, const int* blk_begin, int n_units, int total_blocks,
+                                  cudaStream_t st);
+cudaError_t launch_level_sum_batched(const SumUnit* units, int n_units, cudaStream_t st);
+cudaError_t launch_fill_batched(const FillUnit* units, int n_units, cudaStream_t st);
 
 }  // namespace nqs
