@@ -217,8 +217,10 @@ def run_reference(args):
             vals.append(r)
     v = sum(x["value"] for x in vals) / len(vals)
     from oracle import csim
+    from oracle.expansion import term_count
+    n_terms = term_count(w.n_noise, level)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "terms/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * 1771 / v if v else None,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * n_terms / v if v else None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
             "data": "synthetic", "config": {"workload": args.workload, "description": desc},
             "cpu_baseline": {"value": v, "unit": "terms/s", "cores": csim.lib().nqso_num_threads(),

@@ -240,6 +240,83 @@ size_t nqs_reduced_matrix_scratch_bytes(int n);
 #define NQS_NOALLOC_MAX_QUBITS 34
 int nqs_reduced_matrix_noalloc(const void* phi, const void* chi, int n, int qubit, double* R_out, void* stream);
 
+/* ---- chosen site sets ------------------------------------------------------
+ * W(S) for a set of noise sites S = {s_1 < ... < s_k}, k <= 3: the sum of the
+ * term values X over every choice of kept non-dominant factor at the sites of
+ * S (dominant factor elsewhere) -- the summand of T_k grouped by site set
+ * (Sec. IV, Algorithm 1's inner loop over factor tuples).
+ * nqs_prepare_sets runs the backward sweep from v and a forward sweep from
+ * psi, keeping phi_s and chi_s for every site (2N + 14 device states); it must
+ * precede nqs_eval_sets and be repeated after nqs_prepare_noise.
+ * nqs_eval_sets: `sets` is m x k site indices (ascending within a set),
+ * W_out receives m doubles on the host (the call synchronises `stream`).
+ * Errors: NQS_ERR_ARG (bad k, unordered or out-of-range sites),
+ * NQS_ERR_ORDER (not prepared), NQS_ERR_NOMEM, NQS_ERR_CUDA. */
+int nqs_prepare_sets(nqs_handle h, const nqs_state* psi, const nqs_state* v, void* stream);
+int nqs_eval_sets(nqs_handle h, int k, const int32_t* sets, size_t m, double* W_out, void* stream);
+
+/* ---- proposal network (learned importance sampling) --------------------
+ * A multilayer perceptron: n_in inputs, `hidden_layers` ReLU layers of
+ * `hidden` units, one linear output.  Weights are stored in fp32 (masters)
+ * and used in bf16 by the forward and backward kernels, with fp32
+ * accumulation; training is Adam on the mean squared error.  The paper has
+ * no counterpart: the network proposes which higher-level site sets an
+ * importance-sampled estimate of a level's sum evaluates.
+ * Parameters flatten as, per layer, W (out x in, row-major) then b (out).
+ * X is row-major [batch x n_in] fp32, y is [batch] fp32, device memory. */
+typedef struct nqs_mlp_s* nqs_mlp;
+int nqs_mlp_create(int n_in, int hidden, int hidden_layers, uint64_t seed, nqs_mlp* out);
+size_t nqs_mlp_param_count(nqs_mlp m);
+int nqs_mlp_get_params(nqs_mlp m, float* host, size_t cap);          /* fp32 masters */
+int nqs_mlp_set_params(nqs_mlp m, const float* host, size_t count);
+int nqs_mlp_forward(nqs_mlp m, const float* X, int batch, float* y, void* stream);
+/* loss and gradient (w.r.t. the fp32 masters) of one batch, copied to host */
+int nqs_mlp_loss_grad(nqs_mlp m, const float* X, const float* y, int batch, double* loss, float* grad_host,
+                      size_t cap, void* stream);
+/* `steps` Adam steps on batches drawn (counter-based generator, `seed`)
+ * from the n rows of (X, y); *final_loss = loss of the last batch */
+int nqs_mlp_train(nqs_mlp m, const float* X, const float* y, int n, int batch, int steps, float lr, uint64_t seed,
+                  double* final_loss, void* stream);
+void nqs_mlp_destroy(nqs_mlp m);
+
+/* ---- importance-sampled level sums ------------------------------------------
+ * Site features for the proposal network (host, N x 4 floats, each column
+ * standardised over the sites): the noise's position in the gate sequence,
+ * its qubit, log10 of its noise rate ||M - I||, log10 of its level-1 weight
+ * W1[s] = sum of its level-1 term values. */
+int nqs_site_features(nqs_handle h, const double* W1, float* out);
+/* Training rows for pair scores: for every pair s < t (lexicographic), X row =
+ * features of s then of t (8 floats), y = ln W2[s*N + t] (W2: host N x N,
+ * the level-2 weight of the pair).  *count = N(N-1)/2; nothing is written
+ * when cap < count. */
+int nqs_pair_training_data(nqs_handle h, const float* feats, const double* W2, float* X, float* y, size_t cap,
+                           size_t* count);
+
+typedef struct {
+    double estimate;      /* unbiased estimate of T_level */
+    double stderr_;       /* its standard error (sample variance / samples) */
+    double ess;           /* effective sample size of the proposal weights */
+    uint64_t samples;
+    uint64_t distinct;    /* distinct site sets evaluated */
+    uint64_t n_sets;      /* C(N, level) */
+    double alpha;         /* weight of the uniform part of the proposal */
+    int32_t level;
+    int32_t status;
+} nqs_is_result;
+
+/* Importance-sampled estimate of T_level (level 2 or 3) of the expansion
+ * (Sec. IV's T_u summed by site sets).  The proposal scores a site set by
+ * the network's pair scores (a triple by its three pairs minus the level-1
+ * log weights of its sites), takes the softmax over all C(N, level) sets and
+ * mixes it with the uniform law: q = (1 - alpha) softmax + alpha / C(N, level).
+ * mlp == NULL gives the uniform proposal.  Sets are drawn by inverse-CDF
+ * lookup of SplitMix64 uniforms (seed + draw index), each distinct set is
+ * evaluated once on the GPU (nqs_eval_sets, which needs nqs_prepare_sets),
+ * and estimate = mean of W(S_j) / q(S_j).  feats: host N x 4 from
+ * nqs_site_features; W1: host N level-1 weights.  Synchronises `stream`. */
+int nqs_is_estimate(nqs_handle h, nqs_mlp mlp, int level, uint64_t samples, double alpha, uint64_t seed,
+                    const float* feats, const double* W1, nqs_is_result* out, void* stream);
+
 void nqs_destroy(nqs_handle h);
 const char* nqs_strerror(int code);
 const char* nqs_version(void);

@@ -103,6 +103,7 @@ int nqs_prepare_noise(nqs_handle hh, const nqs_noise* sites, size_t n_sites, uin
     }
     engine_batch_forget(h);
     engine_destroy(*h);
+    sets_destroy(*h);
     h->circ.noises = ns;
     h->factors = fac;
     build_plan(h->circ, h->factors, kTileQubits, h->plan);
@@ -299,11 +300,92 @@ size_t nqs_reduced_matrix_scratch_bytes(int n) {
     return engine_reduced_matrix_scratch_bytes(n);
 }
 
+int nqs_prepare_sets(nqs_handle hh, const nqs_state* psi, const nqs_state* v, void* stream) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return NQS_ERR_ARG;
+    if (!h->prepared) return NQS_ERR_ORDER;
+    int rc = check_state(*h, psi, false);
+    if (rc) return rc;
+    rc = check_state(*h, v, true);
+    if (rc) return rc;
+    return engine_prepare_sets(*h, psi, v, stream);
+}
+
+int nqs_eval_sets(nqs_handle hh, int k, const int32_t* sets, size_t m, double* W_out, void* stream) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !sets || !W_out || k < 1 || k > 3) return NQS_ERR_ARG;
+    if (m == 0) return NQS_OK;
+    return engine_eval_sets(*h, k, sets, m, W_out, stream);
+}
+
+int nqs_mlp_create(int n_in, int hidden, int hidden_layers, uint64_t seed, nqs_mlp* out) {
+    if (!out) return NQS_ERR_ARG;
+    Mlp* m = nullptr;
+    int rc = mlp_create(n_in, hidden, hidden_layers, seed, &m);
+    if (rc == NQS_OK) *out = reinterpret_cast<nqs_mlp>(m);
+    return rc;
+}
+
+size_t nqs_mlp_param_count(nqs_mlp m) { return m ? mlp_n_params(reinterpret_cast<Mlp*>(m)) : 0; }
+
+int nqs_mlp_get_params(nqs_mlp m, float* host, size_t cap) {
+    if (!m || !host) return NQS_ERR_ARG;
+    return mlp_get_params(reinterpret_cast<Mlp*>(m), host, cap);
+}
+
+int nqs_mlp_set_params(nqs_mlp m, const float* host, size_t count) {
+    if (!m || !host) return NQS_ERR_ARG;
+    return mlp_set_params(reinterpret_cast<Mlp*>(m), host, count);
+}
+
+int nqs_mlp_forward(nqs_mlp m, const float* X, int batch, float* y, void* stream) {
+    if (!m || !X || !y || batch < 1) return NQS_ERR_ARG;
+    return mlp_forward(reinterpret_cast<Mlp*>(m), X, batch, y, stream);
+}
+
+int nqs_mlp_loss_grad(nqs_mlp m, const float* X, const float* y, int batch, double* loss, float* grad_host, size_t cap,
+                      void* stream) {
+    if (!m || !X || !y || !loss || !grad_host || batch < 1) return NQS_ERR_ARG;
+    return mlp_loss_grad(reinterpret_cast<Mlp*>(m), X, y, batch, loss, grad_host, cap, stream);
+}
+
+int nqs_mlp_train(nqs_mlp m, const float* X, const float* y, int n, int batch, int steps, float lr, uint64_t seed,
+                  double* final_loss, void* stream) {
+    if (!m || !X || !y || !(lr > 0.f)) return NQS_ERR_ARG;
+    return mlp_train(reinterpret_cast<Mlp*>(m), X, y, n, batch, steps, lr, seed, final_loss, stream);
+}
+
+void nqs_mlp_destroy(nqs_mlp m) { mlp_destroy(reinterpret_cast<Mlp*>(m)); }
+
+int nqs_site_features(nqs_handle hh, const double* W1, float* out) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !W1 || !out) return NQS_ERR_ARG;
+    if (!h->prepared) return NQS_ERR_ORDER;
+    return site_features(*h, W1, out);
+}
+
+int nqs_pair_training_data(nqs_handle hh, const float* feats, const double* W2, float* X, float* y, size_t cap,
+                           size_t* count) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !feats || !W2 || !count || (cap && (!X || !y))) return NQS_ERR_ARG;
+    if (!h->prepared) return NQS_ERR_ORDER;
+    return pair_training_data(*h, feats, W2, X, y, cap, count);
+}
+
+int nqs_is_estimate(nqs_handle hh, nqs_mlp mlp, int level, uint64_t samples, double alpha, uint64_t seed,
+                    const float* feats, const double* W1, nqs_is_result* out, void* stream) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !out || (mlp && (!feats || !W1)) || (!W1)) return NQS_ERR_ARG;
+    if (!h->prepared) return NQS_ERR_ORDER;
+    return is_estimate(*h, reinterpret_cast<Mlp*>(mlp), level, samples, alpha, seed, feats, W1, out, stream);
+}
+
 void nqs_destroy(nqs_handle hh) {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h) return;
     engine_batch_forget(h);
     engine_destroy(*h);
+    sets_destroy(*h);
     delete h;
 }
 

@@ -34,27 +34,10 @@
 
 namespace nqs {
 
-namespace {
 
 int cuda_err(cudaError_t e) { return e == cudaSuccess ? NQS_OK : NQS_ERR_CUDA; }
 
-// Matrix table builder (float2 for sweeps, complex128 for finishers).
-struct Tables {
-    std::vector<float2> mats;
-    std::vector<double> kmats;     // per site: K_0..K_3, 8 doubles each
-    int add(const cd* m, int cnt, bool adjoint, int dim) {
-        int off = (int)mats.size();
-        for (int r = 0; r < dim; ++r)
-            for (int c = 0; c < dim; ++c) {
-                cd v = adjoint ? std::conj(m[dim * c + r]) : m[dim * r + c];
-                mats.push_back(make_float2((float)v.real(), (float)v.imag()));
-            }
-        (void)cnt;
-        return off;
-    }
-};
 
-enum RunType { RT_IDEAL, RT_BWD, RT_FWD };
 
 // Program of one register-resident launch, appended to `prog` (16-byte
 // words): the phases, one 16-byte record per operation, then the matrices.
@@ -65,9 +48,7 @@ enum RunType { RT_IDEAL, RT_BWD, RT_FWD };
 // free position of each residue class mod 5 (the bank bits of the swizzled
 // transpose buffer) and the warp bits to the rest.  Returns the offsets
 // (in words) of the operations and matrices and the phase count.
-struct ProgInfo {
-    int words_begin = 0, n_words = 0, ops_word = 0, mats_word = 0, n_phases = 0;
-};
+
 
 ProgInfo build_program(const std::vector<DevOp>& dops, int off, int n, int RB, const Tables& tab,
                        std::vector<uint4>& prog) {
@@ -268,8 +249,6 @@ Run make_run(const Plan& plan, const std::vector<PassSpec>& segs, RunType rt, bo
     }
     return run;
 }
-
-}  // namespace
 
 // ------------------------------------------------------------------ schedule
 namespace {
@@ -790,7 +769,8 @@ int run_launch(Handle& h, Engine& E, const Launch& l, cudaStream_t st) {
         case L_FILL: return cuda_err(launch_basis_fill(l.dst, dim, l.bits, fill_grid, st));
         case L_COPY:
             return cuda_err(cudaMemcpyAsync(l.dst, l.src, dim * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-        case L_REDUCE2: return cuda_err(launch_reduce2x2(l.src, l.dst, h.plan.n, 0, E.partials, l.grid, st));
+        case L_REDUCE2:   // bits holds the qubit
+            return cuda_err(launch_reduce2x2(l.src, l.dst, h.plan.n, (int)l.bits, E.partials, l.grid, st));
         case L_SUM:
             return cuda_err(launch_level_sum(E.term_vals, E.level_off_dev, E.eff_level, E.res_dev, E.bound, E.n_terms,
                                              E.err_dev, st));

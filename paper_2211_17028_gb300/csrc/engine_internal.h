@@ -89,6 +89,34 @@ struct Engine {
 };
 
 
+// Matrix table builder (float2 for sweeps, complex128 for finishers).
+struct Tables {
+    std::vector<float2> mats;
+    std::vector<double> kmats;     // per site: K_0..K_3, 8 doubles each
+    int add(const cd* m, int cnt, bool adjoint, int dim) {
+        int off = (int)mats.size();
+        for (int r = 0; r < dim; ++r)
+            for (int c = 0; c < dim; ++c) {
+                cd v = adjoint ? std::conj(m[dim * c + r]) : m[dim * r + c];
+                mats.push_back(make_float2((float)v.real(), (float)v.imag()));
+            }
+        (void)cnt;
+        return off;
+    }
+};
+
+enum RunType { RT_IDEAL, RT_BWD, RT_FWD };
+
+struct ProgInfo {
+    int words_begin = 0, n_words = 0, ops_word = 0, mats_word = 0, n_phases = 0;
+};
+
+int cuda_err(cudaError_t e);
+ProgInfo build_program(const std::vector<DevOp>& dops, int off, int n, int RB, const Tables& tab,
+                       std::vector<uint4>& prog);
+Run make_run(const Plan& plan, const std::vector<PassSpec>& segs, RunType rt, bool reduce, bool spawn,
+             bool level0_only, const std::vector<Factors>& fac, Tables& tab, std::vector<DevOp>& dops);
+
 // schedule construction and execution (engine.cu)
 int engine_init(Engine& E);
 void engine_release(Engine& E, void* stream);

@@ -142,6 +142,15 @@ int factor_noise(const NoiseSite& s, bool prune_zero_rank, Factors& f) {
         for (int e = 0; e < 16; ++e) rest[e] += t[e];
     }
     f.norm_rest = spectral_norm4(rest);
+    {
+        Mat4 m{};
+        for (const auto& e : s.kraus) {
+            Mat4 t = kron_conj(e);
+            for (int i = 0; i < 16; ++i) m[i] += t[i];
+        }
+        for (int i = 0; i < 4; ++i) m[5 * i] -= cd(1);
+        f.rate = spectral_norm4(m);
+    }
     return NQS_OK;
 }
 

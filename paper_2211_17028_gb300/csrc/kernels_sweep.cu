@@ -237,7 +237,7 @@ __device__ __forceinline__ void site_reg(const PassArgs& P, const OpRec& op, con
     const int fl = op.flags;
     const float2 k0 = m[0], k1 = m[1], k2 = m[2], k3 = m[3];
     const float2* phi = (fl & FL_REDUCE) ? P.ckpt[op.site] : nullptr;
-    float2* save = (fl & FL_SAVE) ? P.ckpt[op.site] : nullptr;
+    float2* save = (fl & FL_SAVE) ? P.ckpt[op.site] : (fl & FL_SAVE_FWD) ? P.ckpt_fwd[op.site] : nullptr;
     float rr[S][8];
 #pragma unroll
     for (int s = 0; s < S; ++s)
@@ -257,7 +257,7 @@ __device__ __forceinline__ void site_reg(const PassArgs& P, const OpRec& op, con
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             const float2 a = x[s][r], b = x[s][r1];
-            if ((fl & FL_SAVE) && s == 0) {
+            if ((fl & (FL_SAVE | FL_SAVE_FWD)) && s == 0) {
                 __stcs(save + g0, a);
                 __stcs(save + g1, b);
             }

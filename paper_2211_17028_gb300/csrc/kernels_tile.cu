@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kThreads) tile_pass_kernel(const PassArgs P) {
                 const float2 k0 = P.mats[op.mat], k1 = P.mats[op.mat + 1];
                 const float2 k2 = P.mats[op.mat + 2], k3 = P.mats[op.mat + 3];
                 const float2* phi = (fl & FL_REDUCE) ? P.ckpt[op.site] : nullptr;
-                float2* save = (fl & FL_SAVE) ? P.ckpt[op.site] : nullptr;
+                float2* save = (fl & FL_SAVE) ? P.ckpt[op.site] : (fl & FL_SAVE_FWD) ? P.ckpt_fwd[op.site] : nullptr;
                 float r[S][8];
 #pragma unroll
                 for (int s = 0; s < S; ++s)
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kThreads) tile_pass_kernel(const PassArgs P) {
                     for (int s = 0; s < S; ++s) {
                         float2 x0 = tile[s * T + j0], x1 = tile[s * T + j1];
                         // phi_s excludes the site's own factor: save before applying K_0^dagger
-                        if ((fl & FL_SAVE) && s == 0) {
+                        if ((fl & (FL_SAVE | FL_SAVE_FWD)) && s == 0) {
                             __stcs(save + g0, x0);
                             __stcs(save + g1, x1);
                         }

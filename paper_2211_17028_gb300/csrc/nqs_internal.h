@@ -51,6 +51,7 @@ struct Factors {
     int keep[3] = {1, 2, 3};// their factor indices
     double norm_dom;        // ||U_0 (x) V_0||_2 = d_0 * ... (spectral norm of M')
     double norm_rest;       // ||sum_{i>=1} U_i (x) V_i||_2
+    double rate;            // noise rate ||M - I||_2 (Sec. IV)
 };
 
 // Returns NQS_OK, NQS_ERR_NOT_CPTP or NQS_ERR_NOT_DOMINANT.
@@ -99,7 +100,8 @@ void build_plan(const Circuit& c, const std::vector<Factors>& f, int tile_qubits
 std::vector<PassSpec> segment(const Plan& p, bool cut_after_sites, int max_sites_per_pass, int max_ops_per_pass);
 
 // ------------------------------------------------------------------- handle
-struct Engine;   // device-side state (engine.cu)
+struct Engine;     // device-side state (engine.cu)
+struct SetsState;  // checkpoints for site-set evaluation (sets.cu)
 
 struct Handle {
     Circuit circ;
@@ -107,6 +109,7 @@ struct Handle {
     std::vector<Factors> factors;
     Plan plan;
     Engine* eng = nullptr;
+    SetsState* sets = nullptr;
     bool profiling = false;
     nqs_kernel_stats stats[5] = {};
 };
@@ -118,6 +121,16 @@ int engine_term_values(Handle& h, double* out, size_t cap, size_t* count);
 int engine_batch_fidelity(Handle** hs, size_t count, const nqs_state* psis, const nqs_state* vs, const int* levels,
                           nqs_result* outs, void* stream);
 void engine_batch_forget(Handle* h);   // drop a cached batch plan that uses h
+int engine_prepare_sets(Handle& h, const nqs_state* psi, const nqs_state* v, void* stream);
+int engine_eval_sets(Handle& h, int k, const int* sets, size_t m, double* W_out, void* stream);
+void sets_destroy(Handle& h);
+// learned importance sampling (is.cpp)
+struct Mlp;
+int site_features(const Handle& h, const double* W1, float* out);
+int pair_training_data(const Handle& h, const float* feats, const double* W2, float* X, float* y, size_t cap,
+                       size_t* count);
+int is_estimate(Handle& h, Mlp* mlp, int level, unsigned long long samples, double alpha, unsigned long long seed,
+                const float* feats, const double* W1, nqs_is_result* out, void* stream);
 void engine_destroy(Handle& h);
 uint64_t engine_workspace_bytes(const Handle& h);
 uint64_t engine_upload_bytes(const Handle& h);
@@ -125,6 +138,20 @@ uint64_t engine_launches_per_call(const Handle& h);
 int engine_reduced_matrix(const void* phi, const void* chi, int n, int qubit, double* R_out,
                           void* scratch, size_t scratch_bytes, void* stream);
 size_t engine_reduced_matrix_scratch_bytes(int n);
+
+// proposal network (mlp.cu)
+struct Mlp;
+int mlp_create(int n_in, int hidden, int layers, unsigned long long seed, Mlp** out);
+void mlp_destroy(Mlp* m);
+size_t mlp_n_params(const Mlp* m);
+int mlp_n_in(const Mlp* m);
+int mlp_get_params(Mlp* m, float* host, size_t cap);
+int mlp_set_params(Mlp* m, const float* host, size_t count);
+int mlp_forward(Mlp* m, const float* X, int B, float* y, void* stream);
+int mlp_loss_grad(Mlp* m, const float* X, const float* y, int B, double* loss, float* grad_host, size_t cap,
+                  void* stream);
+int mlp_train(Mlp* m, const float* X, const float* y, int n, int batch, int steps, float lr, unsigned long long seed,
+              double* final_loss, void* stream);
 
 // allocator (capi.cpp)
 void* dev_alloc(size_t bytes, void* stream);

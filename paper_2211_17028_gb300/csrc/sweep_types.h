@@ -24,6 +24,7 @@ enum : int {
     FL_SPAWN = 2,     // write K_i x for the kept non-dominant factors
     FL_SAVE = 4,      // store the state as phi_site (before K_0^dagger)
     FL_APPLY = 8,     // apply the site's K_0 (K_0^dagger backwards) after the other actions
+    FL_SAVE_FWD = 16, // store the state as chi_site (forward checkpoint, before K_0)
     FL_KDIAG = 32     // K_0 is diagonal
 };
 
@@ -78,6 +79,7 @@ struct PassArgs {
     const float2* in[3];
     float2* out[3];
     float2* const* ckpt;   // phi_s slots
+    float2* const* ckpt_fwd;   // chi_s slots (forward checkpoints)
     float2* spawn[9];
     double* partials;      // [(event * S + state) * grid + block][8]
     int* err;              // device status word (bounded waits that gave up)

@@ -59,6 +59,15 @@ class nqs_result(ctypes.Structure):
                 "level": self.level, "status": self.status}
 
 
+class nqs_is_result(ctypes.Structure):
+    _fields_ = [("estimate", ctypes.c_double), ("stderr_", ctypes.c_double), ("ess", ctypes.c_double),
+                ("samples", ctypes.c_uint64), ("distinct", ctypes.c_uint64), ("n_sets", ctypes.c_uint64),
+                ("alpha", ctypes.c_double), ("level", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+    def to_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class nqs_info(ctypes.Structure):
     _fields_ = [("n_qubits", ctypes.c_int32), ("n_gates", ctypes.c_int32), ("n_sites", ctypes.c_int32),
                 ("n_ops", ctypes.c_int32), ("n_passes", ctypes.c_int32), ("tile_qubits", ctypes.c_int32),
@@ -103,6 +112,30 @@ _SIGS = {
     "nqs_reduced_matrix_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int]),
     "nqs_reduced_matrix_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                   ctypes.c_void_p, ctypes.c_void_p]),
+    "nqs_prepare_sets": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(nqs_state), ctypes.POINTER(nqs_state),
+                                        ctypes.c_void_p]),
+    "nqs_eval_sets": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                     ctypes.c_void_p, ctypes.c_void_p]),
+    "nqs_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+    "nqs_mlp_param_count": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "nqs_mlp_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "nqs_mlp_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "nqs_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "nqs_mlp_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_size_t,
+                                         ctypes.c_void_p]),
+    "nqs_mlp_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_float, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.c_void_p]),
+    "nqs_mlp_destroy": (None, [ctypes.c_void_p]),
+    "nqs_site_features": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "nqs_pair_training_data": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "nqs_is_estimate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
+                                       ctypes.c_double, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.POINTER(nqs_is_result), ctypes.c_void_p]),
     "nqs_destroy": (None, [ctypes.c_void_p]),
     "nqs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "nqs_version": (ctypes.c_char_p, []),
@@ -326,6 +359,107 @@ def nqs_reduced_matrix_noalloc(phi, chi, n, qubit, r_out, stream=None):
 
 def nqs_reduced_matrix_scratch_bytes(n):
     return int(_lib().nqs_reduced_matrix_scratch_bytes(n))
+
+
+def nqs_prepare_sets(h, psi, v, stream=None):
+    ps, vs = _as_state(psi), _as_state(v)
+    _check(_lib().nqs_prepare_sets(h, ctypes.byref(ps), ctypes.byref(vs), _stream_ptr(stream)), "nqs_prepare_sets")
+
+
+def nqs_eval_sets(h, sets, stream=None):
+    """sets: integer array [m x k] of ascending site indices; returns W [m]."""
+    import numpy as np
+    s = np.ascontiguousarray(sets, dtype=np.int32)
+    if s.ndim == 1:
+        s = s[:, None]
+    W = np.zeros(s.shape[0], dtype=np.float64)
+    _check(_lib().nqs_eval_sets(h, s.shape[1], s.ctypes.data, s.shape[0], W.ctypes.data, _stream_ptr(stream)),
+           "nqs_eval_sets")
+    return W
+
+
+def _ptr(x):
+    return ctypes.c_void_p(x if isinstance(x, int) else x.data_ptr())
+
+
+def nqs_mlp_create(n_in, hidden=256, hidden_layers=3, seed=0):
+    m = ctypes.c_void_p()
+    _check(_lib().nqs_mlp_create(n_in, hidden, hidden_layers, seed, ctypes.byref(m)), "nqs_mlp_create")
+    return m
+
+
+def nqs_mlp_param_count(m):
+    return int(_lib().nqs_mlp_param_count(m))
+
+
+def nqs_mlp_get_params(m):
+    import numpy as np
+    out = np.zeros(nqs_mlp_param_count(m), dtype=np.float32)
+    _check(_lib().nqs_mlp_get_params(m, out.ctypes.data, out.size), "nqs_mlp_get_params")
+    return out
+
+
+def nqs_mlp_set_params(m, params):
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(_lib().nqs_mlp_set_params(m, p.ctypes.data, p.size), "nqs_mlp_set_params")
+
+
+def nqs_mlp_forward(m, X, y, stream=None):
+    """X: [batch x n_in] fp32 CUDA tensor; y: [batch] fp32 CUDA tensor (output)."""
+    _check(_lib().nqs_mlp_forward(m, _ptr(X), X.shape[0], _ptr(y), _stream_ptr(stream)), "nqs_mlp_forward")
+
+
+def nqs_mlp_loss_grad(m, X, y, stream=None):
+    import numpy as np
+    g = np.zeros(nqs_mlp_param_count(m), dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(_lib().nqs_mlp_loss_grad(m, _ptr(X), _ptr(y), X.shape[0], ctypes.byref(loss), g.ctypes.data, g.size,
+                                    _stream_ptr(stream)), "nqs_mlp_loss_grad")
+    return loss.value, g
+
+
+def nqs_mlp_train(m, X, y, batch, steps, lr, seed=0, stream=None):
+    loss = ctypes.c_double()
+    _check(_lib().nqs_mlp_train(m, _ptr(X), _ptr(y), X.shape[0], batch, steps, lr, seed, ctypes.byref(loss),
+                                _stream_ptr(stream)), "nqs_mlp_train")
+    return loss.value
+
+
+def nqs_mlp_destroy(m):
+    _lib().nqs_mlp_destroy(m)
+
+
+def nqs_site_features(h, W1):
+    import numpy as np
+    w = np.ascontiguousarray(W1, dtype=np.float64)
+    out = np.zeros((w.size, 4), dtype=np.float32)
+    _check(_lib().nqs_site_features(h, w.ctypes.data, out.ctypes.data), "nqs_site_features")
+    return out
+
+
+def nqs_pair_training_data(h, feats, W2):
+    import numpy as np
+    f = np.ascontiguousarray(feats, dtype=np.float32)
+    w2 = np.ascontiguousarray(W2, dtype=np.float64)
+    cnt = ctypes.c_size_t()
+    _check(_lib().nqs_pair_training_data(h, f.ctypes.data, w2.ctypes.data, None, None, 0, ctypes.byref(cnt)),
+           "nqs_pair_training_data")
+    X = np.zeros((cnt.value, 8), dtype=np.float32)
+    y = np.zeros(cnt.value, dtype=np.float32)
+    _check(_lib().nqs_pair_training_data(h, f.ctypes.data, w2.ctypes.data, X.ctypes.data, y.ctypes.data, cnt.value,
+                                         ctypes.byref(cnt)), "nqs_pair_training_data")
+    return X, y
+
+
+def nqs_is_estimate(h, mlp, level, samples, alpha, seed, feats, W1, stream=None):
+    import numpy as np
+    f = None if feats is None else np.ascontiguousarray(feats, dtype=np.float32)
+    w1 = np.ascontiguousarray(W1, dtype=np.float64)
+    out = nqs_is_result()
+    _check(_lib().nqs_is_estimate(h, mlp, level, samples, alpha, seed, None if f is None else f.ctypes.data,
+                                  w1.ctypes.data, ctypes.byref(out), _stream_ptr(stream)), "nqs_is_estimate")
+    return out.to_dict()
 
 
 def nqs_destroy(h):

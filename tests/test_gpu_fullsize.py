@@ -1,0 +1,138 @@
+"""Parity at full size: the 30-qubit QAOA workload at level 2, run through
+the C ABI in the launch configuration the benchmark times (8 GiB states).
+
+The oracle cannot contract the 1771 networks of 30 qubits in seconds, so it
+computes sampled outputs one by one with the help of a property of this
+workload: v = U|psi> and every noise is depolarizing, whose dominant factors
+are multiples of the identity (Sec. IV: U_0 = c I, V_0 = c' I).  With every
+other site on its dominant factor, the two networks of a term with insertions
+at sites s < t reduce to
+
+    a = prod_{u not in S} c_u  * <chi_t| U_j  W  U_i |chi_s>
+    b = prod_{u not in S} c'_u * conj(<chi_t| conj(V_j) W conj(V_i) |chi_s>)
+
+(chi_s = gates before site s applied to psi, W = gates between s and t), so
+the oracle needs only the prefix of the circuit up to the sampled sites,
+swept in FP64 by its C state-vector code.  Checked: T_0, the level-1 sums of
+the first three sites and the level-2 sum of the first pair, each within
+1e-5 F and, as these sums are far below F, within 1% of itself; T_1 equals the sum of all level-1 site sums; F = T_0 + T_1 + T_2."""
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import csim
+from oracle import expansion as OEX
+from oracle import gates as G
+from oracle import ir as OIR
+
+from _gpu_util import REL_TOL, site_sets
+
+pytestmark = pytest.mark.gpu
+
+
+def _gate_ops(c, e0, e1):
+    """Gates among events [e0, e1) as one op list (noise events skipped)."""
+    ops = csim.OpList()
+    for e, (kind, idx) in enumerate(OIR.events(c)):
+        if e0 <= e < e1 and kind == "gate":
+            name, qs, ps = c.gates[idx]
+            ops.add(qs, G.gate_matrix(name, ps))
+    return ops
+
+
+def _one(q, m):
+    ops = csim.OpList()
+    ops.add((q,), m)
+    return ops
+
+
+def _identity_scale(m):
+    assert abs(m[0, 1]) < 1e-12 and abs(m[1, 0]) < 1e-12 and abs(m[0, 0] - m[1, 1]) < 1e-12
+    return complex(m[0, 0])
+
+
+def test_qaoa30_level2_sampled_terms():
+    import torch
+    from paper_2211_17028_gb300 import nqs
+    torch.cuda.set_device(0)
+    nqs.use_torch_allocator()
+    w = W.c3_qaoa30()
+    text = W.to_ir_text(w)
+    circ = nqs.NoisyCircuit(text)
+    res = circ.fidelity(nqs.basis(0), nqs.ideal(), 2)
+    recs = nqs.nqs_enumerate_terms(circ.h, 2)
+    vals = circ.term_values()
+    circ.close()
+    torch.cuda.empty_cache()
+    assert res["status"] == 0 and res["n_terms"] == 1771
+    F = res["F"]
+    got = site_sets(recs, vals)
+    assert abs(F - sum(res["T"])) <= 1e-12 * F
+    assert abs(res["T"][1] - sum(got[(s,)] for s in range(w.n_noise))) <= 1e-9 * F
+
+    c = OIR.parse(text)
+    fac = OEX.prepared_factors(c)
+    cu = [_identity_scale(f[1][0]) for f in fac]
+    cv = [_identity_scale(f[2][0]) for f in fac]
+    ev = {idx: e for e, (kind, idx) in enumerate(OIR.events(c)) if kind == "noise"}
+
+    def rest(S):
+        a = b = 1.0
+        for u in range(len(fac)):
+            if u not in S:
+                a, b = a * cu[u], b * cv[u]
+        return a * b
+
+    T0 = rest(())
+    assert abs(res["T"][0] - T0.real) <= REL_TOL * F, (res["T"][0], T0)
+
+    n = c.n
+    chi = np.zeros(1 << n, dtype=np.complex128)
+    chi[0] = 1.0
+    pos = 0
+    states = {}
+    for s in range(3):
+        csim.apply_ops(n, chi, _gate_ops(c, pos, ev[s]))
+        pos = ev[s]
+        q = c.noises[s][1]
+        W1 = 0.0
+        for i in (1, 2, 3):
+            x = chi.copy()
+            csim.apply_ops(n, x, _one(q, fac[s][1][i]))
+            a = csim.inner(n, chi, x)
+            x[:] = chi
+            csim.apply_ops(n, x, _one(q, fac[s][2][i].conj()))
+            b = csim.inner(n, chi, x).conjugate()
+            del x
+            W1 += (a * b).real
+        W1 *= rest((s,)).real
+        assert abs(got[(s,)] - W1) <= REL_TOL * F, (s, got[(s,)], W1)
+        # the sums are far below F here: also hold each to 1% of itself
+        assert abs(got[(s,)] - W1) <= 1e-2 * W1, (s, got[(s,)], W1)
+        if s < 2:
+            states[s] = chi.copy()
+    del chi
+    # level 2, sites (0, 1)
+    q0, q1 = c.noises[0][1], c.noises[1][1]
+    between = _gate_ops(c, ev[0], ev[1])
+    W2 = 0.0
+    for i in (1, 2, 3):
+        amps = {}
+        for side in (1, 2):
+            y = states[0].copy()
+            m0 = fac[0][side][i] if side == 1 else fac[0][side][i].conj()
+            csim.apply_ops(n, y, _one(q0, m0))
+            csim.apply_ops(n, y, between)
+            for j in (1, 2, 3):
+                z = y.copy()
+                m1 = fac[1][side][j] if side == 1 else fac[1][side][j].conj()
+                csim.apply_ops(n, z, _one(q1, m1))
+                amps[(side, j)] = csim.inner(n, states[1], z)
+                del z
+            del y
+        for j in (1, 2, 3):
+            W2 += (amps[(1, j)] * amps[(2, j)].conjugate()).real
+    W2 *= rest((0, 1)).real
+    assert abs(got[(0, 1)] - W2) <= REL_TOL * F, (got[(0, 1)], W2)
+    assert abs(got[(0, 1)] - W2) <= 1e-2 * W2, (got[(0, 1)], W2)
