@@ -179,9 +179,46 @@ typedef struct {
     uint64_t workspace_bytes;   /* device bytes held by the handle */
     uint64_t upload_bytes;      /* host-to-device bytes of the last schedule build */
     uint64_t launches_per_call; /* kernels launched by one nqs_fidelity call */
+    int32_t ckpt_spacing;       /* sites per checkpoint block of the current schedule (0: every site) */
+    int32_t n_states;           /* 2^n-amplitude state buffers held by the current schedule */
 } nqs_info;
 
 int nqs_get_info(nqs_handle h, nqs_info* out);
+
+/* ---- execution options ----------------------------------------------------
+ * Choices of this library with no counterpart in the paper; value 0 restores
+ * the automatic choice.  A change takes effect at the next call (the schedule
+ * is rebuilt).
+ *   NQS_OPT_CKPT_SPACING  sites per checkpoint block.  Automatic: phi_s is kept
+ *       at every noise site when those states fit in device memory; otherwise
+ *       (levels <= 2) it is kept at the last site of each block of k sites and
+ *       a block's phi are recomputed from there whenever a sweep enters the
+ *       block, with k chosen to hold the fewest states.  1 <= k < N forces
+ *       blocks of k sites (levels <= 2, else NQS_ERR_UNSUPPORTED at the call);
+ *       k >= N keeps every site.
+ *   NQS_OPT_SWEEP_RB      register qubits per thread of multi-state sweep
+ *       passes: 3 (512-thread blocks) or 4 (256-thread blocks).
+ *   NQS_OPT_MAX_OPS       fused operations per pass, 8..160 (default 96).
+ *   NQS_OPT_MAX_SITES     noise sites per pass, 1..8 (default 4).
+ * NQS_ERR_ARG for an unknown option or a value out of range; NQS_ERR_ORDER
+ * for the two segmentation options before nqs_prepare_noise. */
+#define NQS_OPT_CKPT_SPACING 1
+#define NQS_OPT_SWEEP_RB 2
+#define NQS_OPT_MAX_OPS 3
+#define NQS_OPT_MAX_SITES 4
+
+int nqs_set_option(nqs_handle h, int option, int64_t value);
+int nqs_get_option(nqs_handle h, int option, int64_t* value);
+
+/* Time candidate execution options on this handle and keep the fastest:
+ * register qubits of multi-state passes (3, 4) and operations per pass
+ * (64, 96, 128), each candidate timed by CUDA events over `trials` calls of
+ * nqs_fidelity(h, psi, v, level) on `stream` after one warm-up call.  The
+ * chosen values are readable with nqs_get_option; `out` (may be NULL)
+ * receives the result of the last timed call.  Checkpoint spacing is chosen
+ * by memory, not time (NQS_OPT_CKPT_SPACING). */
+int nqs_autotune(nqs_handle h, const nqs_state* psi, const nqs_state* v, int level, int trials,
+                 nqs_result* out, void* stream);
 
 /* Per-kernel timing of the calls made since profiling was switched on:
  * CUDA events recorded around every sweep-pass launch on the call's stream.

@@ -261,6 +261,113 @@ int nqs_get_info(nqs_handle hh, nqs_info* out) {
     out->workspace_bytes = engine_workspace_bytes(*h);
     out->upload_bytes = engine_upload_bytes(*h);
     out->launches_per_call = engine_launches_per_call(*h);
+    int n_states = 0;
+    out->ckpt_spacing = engine_spacing(*h, &n_states);
+    out->n_states = n_states;
+    return NQS_OK;
+}
+
+namespace {
+
+void resegment(Handle& h) {
+    const int sites = h.opt_max_sites > 0 ? h.opt_max_sites : 4;
+    const int ops = h.opt_max_ops > 0 ? h.opt_max_ops : 96;
+    h.plan.free_passes = segment(h.plan, false, sites, ops);
+    h.plan.sitecut_passes = segment(h.plan, true, sites, ops);
+}
+
+}  // namespace
+
+int nqs_set_option(nqs_handle hh, int option, int64_t value) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || value < 0) return NQS_ERR_ARG;
+    switch (option) {
+        case NQS_OPT_CKPT_SPACING:
+            if (value > (1 << 20)) return NQS_ERR_ARG;
+            h->opt_spacing = (int)value;
+            break;
+        case NQS_OPT_SWEEP_RB:
+            if (value != 0 && value != 3 && value != 4) return NQS_ERR_ARG;
+            h->opt_rb_multi = (int)value;
+            break;
+        case NQS_OPT_MAX_OPS:
+        case NQS_OPT_MAX_SITES: {
+            if (!h->prepared) return NQS_ERR_ORDER;
+            const bool ops = option == NQS_OPT_MAX_OPS;
+            if (value != 0 && (ops ? (value < 8 || value > 160) : (value < 1 || value > 8))) return NQS_ERR_ARG;
+            (ops ? h->opt_max_ops : h->opt_max_sites) = (int)value;
+            resegment(*h);
+            break;
+        }
+        default:
+            return NQS_ERR_ARG;
+    }
+    engine_invalidate(*h);
+    return NQS_OK;
+}
+
+int nqs_get_option(nqs_handle hh, int option, int64_t* value) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !value) return NQS_ERR_ARG;
+    switch (option) {
+        case NQS_OPT_CKPT_SPACING: *value = h->opt_spacing; break;
+        case NQS_OPT_SWEEP_RB: *value = h->opt_rb_multi; break;
+        case NQS_OPT_MAX_OPS: *value = h->opt_max_ops; break;
+        case NQS_OPT_MAX_SITES: *value = h->opt_max_sites; break;
+        default: return NQS_ERR_ARG;
+    }
+    return NQS_OK;
+}
+
+int nqs_autotune(nqs_handle hh, const nqs_state* psi, const nqs_state* v, int level, int trials, nqs_result* out,
+                 void* stream) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || trials < 1 || level < 0) return NQS_ERR_ARG;
+    if (!h->prepared) return NQS_ERR_ORDER;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return NQS_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return NQS_ERR_CUDA;
+    }
+    nqs_result res{};
+    // register qubits matter only where multi-state passes run (level >= 2)
+    const int rbs[2] = {3, 4};
+    const int n_rb = level >= 2 ? 2 : 1;
+    const int opss[3] = {64, 96, 128};
+    float best_ms = -1.f;
+    int best_rb = 0, best_ops = 0, rc = NQS_OK;
+    for (int a = 0; a < n_rb && rc == NQS_OK; ++a)
+        for (int b = 0; b < 3 && rc == NQS_OK; ++b) {
+            const int rb = n_rb > 1 ? rbs[a] : 0;
+            if ((rc = nqs_set_option(hh, NQS_OPT_SWEEP_RB, rb)) != NQS_OK) break;
+            if ((rc = nqs_set_option(hh, NQS_OPT_MAX_OPS, opss[b])) != NQS_OK) break;
+            int r = nqs_fidelity(hh, psi, v, level, &res, stream);   // builds the schedule
+            if (r == NQS_ERR_UNSUPPORTED) continue;                   // program does not fit: skip
+            if (r != NQS_OK) {
+                rc = r;
+                break;
+            }
+            if (cudaEventRecord(e0, st) != cudaSuccess) rc = NQS_ERR_CUDA;
+            for (int t = 0; t < trials && rc == NQS_OK; ++t) rc = nqs_fidelity(hh, psi, v, level, &res, stream);
+            if (rc == NQS_OK && cudaEventRecord(e1, st) != cudaSuccess) rc = NQS_ERR_CUDA;
+            if (rc == NQS_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = NQS_ERR_CUDA;
+            float ms = 0.f;
+            if (rc == NQS_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = NQS_ERR_CUDA;
+            if (rc == NQS_OK && (best_ms < 0.f || ms < best_ms)) {
+                best_ms = ms;
+                best_rb = rb;
+                best_ops = opss[b];
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != NQS_OK) return rc;
+    if (best_ms < 0.f) return NQS_ERR_UNSUPPORTED;
+    nqs_set_option(hh, NQS_OPT_SWEEP_RB, best_rb);
+    nqs_set_option(hh, NQS_OPT_MAX_OPS, best_ops);
+    if (out) *out = res;
     return NQS_OK;
 }
 

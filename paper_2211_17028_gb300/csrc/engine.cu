@@ -165,7 +165,8 @@ ProgInfo build_program(const std::vector<DevOp>& dops, int off, int n, int RB, c
 }
 
 Run make_run(const Plan& plan, const std::vector<PassSpec>& segs, RunType rt, bool reduce, bool spawn,
-             bool level0_only, const std::vector<Factors>& fac, Tables& tab, std::vector<DevOp>& dops) {
+             bool level0_only, const std::vector<Factors>& fac, Tables& tab, std::vector<DevOp>& dops,
+             const std::vector<char>* save_only) {
     Run run;
     std::vector<int> fwd_mat(plan.ops.size(), -1), bwd_mat(plan.ops.size(), -1);
     for (size_t i = 0; i < plan.ops.size(); ++i) {
@@ -215,7 +216,7 @@ Run make_run(const Plan& plan, const std::vector<PassSpec>& segs, RunType rt, bo
                 if (rt == RT_IDEAL) {
                     return;   // noiseless sweep: sites are absent
                 } else if (rt == RT_BWD) {
-                    fl = FL_APPLY | FL_SAVE;
+                    fl = FL_APPLY | ((!save_only || (*save_only)[o.site]) ? FL_SAVE : 0);
                 } else {
                     fl = FL_APPLY;
                     bool red = reduce && (!level0_only || first_site_done == 0);
@@ -270,10 +271,12 @@ struct Builder {
     long long dim;
     // device buffers (resolved after allocation)
     float2* main_buf = nullptr;
-    std::vector<float2*> phi;
+    float2* work_buf = nullptr;                     // spaced checkpoints: block recomputation
+    std::vector<float2*> phi;                       // checkpoint table (spaced: ring per site, then boundary per site)
+    std::vector<float2*> bd;                        // spaced checkpoints: phi at the last site of each block
     std::vector<std::vector<float2*>> group_bufs;   // per depth (1..level-1)
     float2** ckpt_dev = nullptr;
-    Run run_ideal, run_bwd;
+    Run run_ideal, run_bwd, run_mat;   // run_mat: per-block phi recomputation (spaced checkpoints)
     std::vector<Run> run_fwd;    // per depth
 
     Builder(Handle& hh, Engine& ee, int lvl) : h(hh), E(ee), plan(hh.plan), level(lvl) {
@@ -318,7 +321,7 @@ struct Builder {
         l.op_index = rp.op_off + start;
         l.rt = rt;
         if (rt) {
-            l.rb = sweep_reg_bits(S);
+            l.rb = (S > 1 && h.opt_rb_multi) ? h.opt_rb_multi : sweep_reg_bits(S);
             ProgInfo pi = build_program(dops, rp.op_off + start, rp.n_ops - start, l.rb, tab, prog);
             l.prog_index = pi.words_begin;
             l.args.prog_words = pi.n_words;
@@ -446,6 +449,102 @@ struct Builder {
             }
         }
     }
+
+    // ---- spaced checkpoints --------------------------------------------
+    // Block c holds the operations after the last site of block c-1 up to
+    // the last site of block c; the operations after the last site form
+    // block nb, which no forward sweep needs.
+    int block_of_op(int op, int k) const {
+        const int N = (int)h.factors.size();
+        const int nb = (N + k - 1) / k;
+        for (int c = 0; c < nb; ++c)
+            if (op <= plan.site_pos[std::min(N, (c + 1) * k) - 1]) return c;
+        return nb;
+    }
+
+    std::vector<int> blocks_of(const Run& run, int k) const {
+        const int N = (int)h.factors.size();
+        std::vector<int> b(run.passes.size());
+        for (size_t p = 0; p < run.passes.size(); ++p)
+            b[p] = run.passes[p].lin.empty() ? (N + k - 1) / k : block_of_op(run.passes[p].lin[0], k);
+        return b;
+    }
+
+    // The group of states spawned at site s sweeps through block c, reducing
+    // against the block's recomputed phi (level 2).
+    void group_block(int s, int c, int k, const std::vector<int>& blk) {
+        const Run& run = run_fwd[1];
+        const int pos = plan.site_pos[s];
+        const int S = h.factors[s].m;
+        if (S == 0) return;
+        float2* bufs[3] = {group_bufs[1][3 * (s % k)], group_bufs[1][3 * (s % k) + 1], group_bufs[1][3 * (s % k) + 2]};
+        for (size_t p = 0; p < run.passes.size(); ++p) {
+            if (blk[p] != c) continue;
+            const RunPass& rp = run.passes[p];
+            int st = 0;
+            while (st < rp.n_ops && rp.lin[st] <= pos) ++st;
+            if (st >= rp.n_ops) continue;
+            add_pass(rp, st, S, (const float2* const*)bufs, bufs, nullptr, 0);
+            add_finish(rp, st, S, [&](int t, int si, int i, FinishDesc& d) {
+                const Factors& ft = h.factors[t];
+                if (i == 0 || i > ft.m) return;
+                int sites[2] = {s, t}, fp[2] = {si, i - 1};
+                d.rank = (long long)ti.rank(2, sites, fp);
+                d.kmat = kmat_off(t, ft.keep[i - 1]);
+            });
+        }
+    }
+
+    // Forward part of a spaced schedule.  For every block b: recompute the
+    // block's phi from its boundary, sweep the main state through the block
+    // (level-0/1 reductions, spawning three states per site), then sweep the
+    // block's spawned groups through every later block, recomputing each
+    // block's phi once for all of them.
+    template <typename RankFn>
+    void spaced_forward(int k, const float2* ext, RankFn main_rank) {
+        const int N = (int)h.factors.size();
+        const int nb = (N + k - 1) / k;
+        const Run& fwd0 = run_fwd[0];
+        const bool groups = level >= 2;
+        const std::vector<int> b0 = blocks_of(fwd0, k), bm = blocks_of(run_mat, k);
+        const std::vector<int> b1 = groups ? blocks_of(run_fwd[1], k) : std::vector<int>();
+        int ring_block = -1;
+        auto materialize = [&](int c) {
+            if (ring_block == c) return;
+            bool first_in = true;
+            for (size_t p = 0; p < run_mat.passes.size(); ++p) {
+                if (bm[p] != c) continue;
+                const float2* in[1] = {first_in ? bd[c] : work_buf};
+                float2* out[1] = {work_buf};
+                add_pass(run_mat.passes[p], 0, 1, in, out, nullptr, 0);
+                first_in = false;
+            }
+            ring_block = c;
+        };
+        bool first = true;
+        for (int b = 0; b < nb; ++b) {
+            materialize(b);
+            for (size_t p = 0; p < fwd0.passes.size(); ++p) {
+                if (b0[p] != b) continue;
+                const RunPass& rp = fwd0.passes[p];
+                const float2* in[1] = {(first && ext) ? ext : main_buf};
+                float2* out[1] = {main_buf};
+                first = false;
+                float2* sp[3];
+                int n_sp = 0;
+                if (groups && rp.spawn_site >= 0)
+                    for (int i = 0; i < 3; ++i) sp[n_sp++] = group_bufs[1][3 * (rp.spawn_site % k) + i];
+                add_pass(rp, 0, 1, in, out, n_sp ? sp : nullptr, n_sp);
+                add_finish(rp, 0, 1, main_rank);
+            }
+            if (!groups) continue;
+            const int s_lo = b * k, s_hi = std::min(N, (b + 1) * k);
+            for (int c = b; c < nb; ++c) {
+                materialize(c);
+                for (int s = s_lo; s < s_hi; ++s) group_block(s, c, k, b1);
+            }
+        }
+    }
 };
 
 }  // namespace
@@ -471,6 +570,27 @@ void engine_release(Engine& E, void* stream) {
     E.launches.clear();
 }
 
+// States held by a schedule that keeps phi every `k` sites: the block
+// boundaries, the ring of one block, main, the recomputation buffer and, at
+// level 2, three spawned states per site of a block.
+static size_t spaced_states(int N, int level, int k) {
+    return (size_t)((N + k - 1) / k) + (size_t)k + 2 + (level >= 2 ? 3 * (size_t)k : 0);
+}
+
+// The block size with the fewest states.
+static int best_spacing(int N, int level) {
+    int best = 1;
+    size_t fewest = spaced_states(N, level, 1);
+    for (int k = 2; k < N; ++k) {
+        const size_t st = spaced_states(N, level, k);
+        if (st < fewest) {
+            fewest = st;
+            best = k;
+        }
+    }
+    return best;
+}
+
 // Build (or reuse) the schedule for this level and state kinds.
 int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* v, int level,
                           void* stream) {
@@ -487,19 +607,7 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
     for (int s = 0; s < N; ++s) m[s] = h.factors[s].m;
     B.ti.build(m, level);
 
-    // runs: the register-resident kernel needs a tile of exactly 12 qubits
     B.rt = plan.k == kMaxTileQ;
-    bool need_ideal = v->kind == NQS_STATE_IDEAL;
-    if (need_ideal) B.run_ideal = make_run(plan, plan.free_passes, RT_IDEAL, false, false, false, h.factors, B.tab, B.dops);
-    if (N > 0) B.run_bwd = make_run(plan, plan.free_passes, RT_BWD, false, false, false, h.factors, B.tab, B.dops);
-    // forward runs per depth d: reduce if d+1 <= level (or level 0 at depth 0), spawn if d+2 <= level
-    int depths = std::max(1, level);
-    for (int d = 0; d < depths; ++d) {
-        bool spawn = d + 2 <= level;
-        bool reduce = (level == 0) ? (d == 0) : (d + 1 <= level);
-        B.run_fwd.push_back(make_run(plan, spawn ? plan.sitecut_passes : plan.free_passes, RT_FWD, reduce && N > 0,
-                                     spawn, level == 0, h.factors, B.tab, B.dops));
-    }
     // finisher factor table (complex128)
     B.tab.kmats.assign((size_t)std::max(N, 1) * 32, 0.0);
     for (int s = 0; s < N; ++s)
@@ -513,31 +621,97 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
         B.tab.kmats[6] = 1.0;
     }
 
-    // state buffers: phi slots, main, group buffers (3 at depth 1, 9 deeper)
+    // state buffers.  Every site keeps its phi when the states fit (or the
+    // option asks for it): phi slots, main, group buffers (3 at depth 1, 9
+    // deeper).  Otherwise (levels <= 2) phi is kept only at the last site of
+    // each block of `spacing` sites and a block's phi are recomputed into a
+    // ring of `spacing` slots whenever a sweep enters the block.
     const size_t sbytes = (size_t)B.dim * sizeof(float2);
     int n_phi = std::max(N, 1);
     int n_group = 0;
     for (int d = 1; d < level; ++d) n_group += (d == 1) ? 3 : 9;
-    size_t n_states = (size_t)n_phi + 1 + n_group;
-    E.buf_bytes = n_states * sbytes;
-    E.buf = dev_alloc(E.buf_bytes, stream);
-    if (!E.buf) {
-        E.buf_bytes = 0;
-        return NQS_ERR_NOMEM;
+    int spacing = 0;
+    if (h.opt_spacing > 0 && h.opt_spacing < N) {
+        if (level > 2) return NQS_ERR_UNSUPPORTED;
+        spacing = h.opt_spacing;
     }
+    size_t n_states = (size_t)n_phi + 1 + n_group;
+    if (spacing == 0) {
+        E.buf_bytes = n_states * sbytes;
+        E.buf = dev_alloc(E.buf_bytes, stream);
+        if (!E.buf) {
+            E.buf_bytes = 0;
+            if (h.opt_spacing != 0 || level > 2 || N < 2) return NQS_ERR_NOMEM;
+            spacing = best_spacing(N, level);
+        }
+    }
+    if (spacing > 0) {
+        n_states = spaced_states(N, level, spacing);
+        E.buf_bytes = n_states * sbytes;
+        E.buf = dev_alloc(E.buf_bytes, stream);
+        if (!E.buf) {
+            E.buf_bytes = 0;
+            return NQS_ERR_NOMEM;
+        }
+    }
+    E.spacing = spacing;
+    E.n_states = n_states;
     float2* base = (float2*)E.buf;
-    for (int s = 0; s < n_phi; ++s) B.phi.push_back(base + (size_t)s * B.dim);
-    B.main_buf = base + (size_t)n_phi * B.dim;
     B.group_bufs.assign(std::max(1, level), {});
-    size_t next = (size_t)n_phi + 1;
-    for (int d = 1; d < level; ++d) {
-        int cnt = (d == 1) ? 3 : 9;
-        for (int i = 0; i < cnt; ++i) B.group_bufs[d].push_back(base + (next++) * B.dim);
+    if (spacing == 0) {
+        for (int s = 0; s < n_phi; ++s) B.phi.push_back(base + (size_t)s * B.dim);
+        B.main_buf = base + (size_t)n_phi * B.dim;
+        size_t next = (size_t)n_phi + 1;
+        for (int d = 1; d < level; ++d) {
+            int cnt = (d == 1) ? 3 : 9;
+            for (int i = 0; i < cnt; ++i) B.group_bufs[d].push_back(base + (next++) * B.dim);
+        }
+    } else {
+        const int nb = (N + spacing - 1) / spacing;
+        size_t next = 0;
+        std::vector<float2*> ring, bd;
+        for (int b = 0; b < nb; ++b) bd.push_back(base + (next++) * B.dim);
+        for (int j = 0; j < spacing; ++j) ring.push_back(base + (next++) * B.dim);
+        B.main_buf = base + (next++) * B.dim;
+        B.work_buf = base + (next++) * B.dim;
+        if (level >= 2)
+            for (int i = 0; i < 3 * spacing; ++i) B.group_bufs[1].push_back(base + (next++) * B.dim);
+        for (int s = 0; s < N; ++s) B.phi.push_back(ring[s % spacing]);
+        for (int s = 0; s < N; ++s) B.phi.push_back(bd[s / spacing]);
+        B.bd = bd;
+    }
+
+    // runs: the register-resident kernel needs a tile of exactly 12 qubits
+    bool need_ideal = v->kind == NQS_STATE_IDEAL;
+    if (need_ideal) B.run_ideal = make_run(plan, plan.free_passes, RT_IDEAL, false, false, false, h.factors, B.tab, B.dops);
+    std::vector<char> block_last;
+    std::vector<PassSpec> spaced_free;
+    if (spacing == 0) {
+        if (N > 0) B.run_bwd = make_run(plan, plan.free_passes, RT_BWD, false, false, false, h.factors, B.tab, B.dops);
+        // forward runs per depth d: reduce if d+1 <= level (or level 0 at depth 0), spawn if d+2 <= level
+        int depths = std::max(1, level);
+        for (int d = 0; d < depths; ++d) {
+            bool spawn = d + 2 <= level;
+            bool reduce = (level == 0) ? (d == 0) : (d + 1 <= level);
+            B.run_fwd.push_back(make_run(plan, spawn ? plan.sitecut_passes : plan.free_passes, RT_FWD,
+                                         reduce && N > 0, spawn, level == 0, h.factors, B.tab, B.dops));
+        }
+    } else {
+        block_last.assign(N, 0);
+        for (int s = 0; s < N; ++s) block_last[s] = ((s + 1) % spacing == 0) || s == N - 1;
+        spaced_free = segment(plan, false, h.opt_max_sites > 0 ? h.opt_max_sites : 4,
+                              h.opt_max_ops > 0 ? h.opt_max_ops : 96, &block_last);
+        // backward: boundary phi only, and the per-block recomputation (every site)
+        B.run_bwd = make_run(plan, spaced_free, RT_BWD, false, false, false, h.factors, B.tab, B.dops, &block_last);
+        B.run_mat = make_run(plan, spaced_free, RT_BWD, false, false, false, h.factors, B.tab, B.dops);
+        const bool spawn = level >= 2;
+        B.run_fwd.push_back(make_run(plan, spawn ? plan.sitecut_passes : spaced_free, RT_FWD, true, spawn,
+                                     level == 0, h.factors, B.tab, B.dops));
+        if (level >= 2)
+            B.run_fwd.push_back(make_run(plan, spaced_free, RT_FWD, true, false, false, h.factors, B.tab, B.dops));
     }
 
     // --- schedule (device pointers to aux tables are patched after layout) ---
-    // Aux layout is decided after the launches are known; PassArgs hold
-    // offsets relative to placeholder pointers that are rebased below.
     B.ckpt_dev = nullptr;
     float2* mainb = B.main_buf;
     const float2* in1[3];
@@ -558,7 +732,7 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
     };
 
     // 1. v (into main), optionally the ideal sweep, then the backward sweep
-    if (N > 0 || true) {
+    {
         bool ext = false;
         const float2* ext_ptr = nullptr;
         if (v->kind == NQS_STATE_IDEAL) {
@@ -585,6 +759,7 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
                 in1[0] = (p == 0 && ext) ? ext_ptr : mainb;
                 out1[0] = mainb;
                 B.add_pass(B.run_bwd.passes[p], 0, 1, in1, out1, nullptr, 0);
+                if (spacing > 0) B.L.back().bd_table = true;
             }
         } else {
             // N = 0: keep v in the single phi slot for the final inner product
@@ -595,13 +770,30 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
             B.L.push_back(l);
         }
     }
+    // finisher ranks of the main forward sweep: level 0 at the first site, level 1 everywhere
+    bool first_red = true;
+    auto main_rank = [&](int t, int s, int i, FinishDesc& d) {
+        (void)s;
+        const Factors& ft = h.factors[t];
+        if (i == 0) {
+            if (first_red) {
+                d.rank = 0;
+                d.kmat = B.kmat_off(t, 0);
+                first_red = false;
+            }
+            return;
+        }
+        if (level < 1 || i > ft.m) return;
+        int site = t, fp = i - 1;
+        d.rank = (long long)B.ti.rank(1, &site, &fp);
+        d.kmat = B.kmat_off(t, ft.keep[i - 1]);
+    };
     // 2. forward sweep from psi, level 0 / 1 reductions, spawns
-    {
+    if (spacing == 0) {
         bool ext = false;
         const float2* ext_ptr = nullptr;
         init_state(psi, mainb, ext, ext_ptr);
         const Run& run = B.run_fwd[0];
-        bool first_red = true;
         for (size_t p = 0; p < run.passes.size(); ++p) {
             const RunPass& rp = run.passes[p];
             in1[0] = (p == 0 && ext) ? ext_ptr : mainb;
@@ -610,22 +802,7 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
             if (level >= 2 && rp.spawn_site >= 0)
                 for (int i = 0; i < 3; ++i) sp.push_back(B.group_bufs[1][i]);
             B.add_pass(rp, 0, 1, in1, out1, sp.empty() ? nullptr : sp.data(), (int)sp.size());
-            B.add_finish(rp, 0, 1, [&](int t, int s, int i, FinishDesc& d) {
-                (void)s;
-                const Factors& ft = h.factors[t];
-                if (i == 0) {
-                    if (first_red) {
-                        d.rank = 0;
-                        d.kmat = B.kmat_off(t, 0);
-                        first_red = false;
-                    }
-                    return;
-                }
-                if (level < 1 || i > ft.m) return;
-                int site = t, fp = i - 1;
-                d.rank = (long long)B.ti.rank(1, &site, &fp);
-                d.kmat = B.kmat_off(t, ft.keep[i - 1]);
-            });
+            B.add_finish(rp, 0, 1, main_rank);
             if (level >= 2 && rp.spawn_site >= 0) {
                 int s = rp.spawn_site;
                 B.dfs_group(1, {}, s, h.factors[s].m, B.group_bufs[1]);
@@ -648,6 +825,11 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
             for (int i = 1; i < 4; ++i) B.descs.push_back({-1, 0, 0});
             B.L.push_back(f);
         }
+    } else {
+        bool ext = false;
+        const float2* ext_ptr = nullptr;
+        init_state(psi, mainb, ext, ext_ptr);
+        B.spaced_forward(spacing, ext ? ext_ptr : nullptr, main_rank);
     }
     {
         Launch l;
@@ -664,7 +846,7 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
     size_t off_ops = 0;
     size_t off_mats = align(off_ops + B.dops.size() * sizeof(DevOp) + 1);
     size_t off_ckpt = align(off_mats + B.tab.mats.size() * sizeof(float2) + 1);
-    size_t off_phase = align(off_ckpt + n_phi * sizeof(float2*));
+    size_t off_phase = align(off_ckpt + B.phi.size() * sizeof(float2*));
     size_t off_err = align(off_phase + B.prog.size() * sizeof(uint4) + 1);
     size_t off_kmat = align(off_err + sizeof(int));
     size_t off_desc = align(off_kmat + B.tab.kmats.size() * sizeof(double));
@@ -704,7 +886,7 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
     };
     up(dops_dev, B.dops.data(), B.dops.size() * sizeof(DevOp));
     up(mats_dev, B.tab.mats.data(), B.tab.mats.size() * sizeof(float2));
-    up(ckpt_dev, B.phi.data(), n_phi * sizeof(float2*));
+    up(ckpt_dev, B.phi.data(), B.phi.size() * sizeof(float2*));
     up(prog_dev, B.prog.data(), B.prog.size() * sizeof(uint4));
     up(E.kmats_dev, B.tab.kmats.data(), B.tab.kmats.size() * sizeof(double));
     up(E.desc_dev, B.descs.data(), B.descs.size() * sizeof(FinishDesc));
@@ -723,7 +905,7 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
         l.args.prog = l.rt ? prog_dev + l.prog_index : nullptr;
         l.args.err = E.err_dev;
         l.args.mats = mats_dev;
-        l.args.ckpt = ckpt_dev;
+        l.args.ckpt = ckpt_dev + (l.bd_table ? N : 0);
         l.args.partials = E.partials;
     }
     E.launches = std::move(B.L);
@@ -875,6 +1057,16 @@ void engine_destroy(Handle& h) {
 }
 
 uint64_t engine_upload_bytes(const Handle& h) { return h.eng ? h.eng->upload_bytes : 0; }
+
+void engine_invalidate(Handle& h) {
+    if (h.eng) h.eng->level = -1;
+    engine_batch_forget(&h);
+}
+
+int engine_spacing(const Handle& h, int* n_states) {
+    *n_states = (h.eng && h.eng->level >= 0) ? (int)h.eng->n_states : 0;
+    return (h.eng && h.eng->level >= 0) ? h.eng->spacing : 0;
+}
 
 uint64_t engine_launches_per_call(const Handle& h) {
     if (!h.eng) return 0;

@@ -47,6 +47,7 @@ struct Launch {
     const float2* src = nullptr;
     unsigned long long bits = 0;
     double bytes = 0;                // algorithmic bytes (pass kernels)
+    bool bd_table = false;           // pass saves through the block-boundary checkpoint table
 };
 
 struct Engine {
@@ -86,6 +87,8 @@ struct Engine {
     bool has_result = false;
     uint64_t upload_bytes = 0;
     uint64_t gen = 0;                // bumped whenever the schedule is rebuilt
+    int spacing = 0;                 // sites per checkpoint block of the current schedule (0: every site)
+    size_t n_states = 0;             // state buffers of the current schedule
 };
 
 
@@ -114,8 +117,11 @@ struct ProgInfo {
 int cuda_err(cudaError_t e);
 ProgInfo build_program(const std::vector<DevOp>& dops, int off, int n, int RB, const Tables& tab,
                        std::vector<uint4>& prog);
+// Device ops of one sweep direction over the passes `segs`.  Backward runs
+// save phi at every site, or only at the sites flagged in `save_only`.
 Run make_run(const Plan& plan, const std::vector<PassSpec>& segs, RunType rt, bool reduce, bool spawn,
-             bool level0_only, const std::vector<Factors>& fac, Tables& tab, std::vector<DevOp>& dops);
+             bool level0_only, const std::vector<Factors>& fac, Tables& tab, std::vector<DevOp>& dops,
+             const std::vector<char>* save_only = nullptr);
 
 // schedule construction and execution (engine.cu)
 int engine_init(Engine& E);

@@ -175,7 +175,8 @@ void build_plan(const Circuit& c, const std::vector<Factors>& f, int tile_qubits
     p.sitecut_passes = segment(p, true, 4, 96);
 }
 
-std::vector<PassSpec> segment(const Plan& p, bool cut_after_sites, int max_sites_per_pass, int max_ops_per_pass) {
+std::vector<PassSpec> segment(const Plan& p, bool cut_after_sites, int max_sites_per_pass, int max_ops_per_pass,
+                              const std::vector<char>* cut_after) {
     std::vector<PassSpec> out;
     const int nops = (int)p.ops.size();
     auto needs = [&](const HostOp& o, int q[2]) {
@@ -221,7 +222,8 @@ std::vector<PassSpec> segment(const Plan& p, bool cut_after_sites, int max_sites
             ++i;
             if (site) {
                 ++sites;
-                if (cut_after_sites || sites >= max_sites_per_pass) break;
+                const bool cut = cut_after && (*cut_after)[p.ops[i - 1].site];
+                if (cut_after_sites || cut || sites >= max_sites_per_pass) break;
             }
         }
         ps.op_end = i;

@@ -97,7 +97,12 @@ struct Plan {
 };
 
 void build_plan(const Circuit& c, const std::vector<Factors>& f, int tile_qubits, Plan& out);
-std::vector<PassSpec> segment(const Plan& p, bool cut_after_sites, int max_sites_per_pass, int max_ops_per_pass);
+// Cut the linear op order into passes whose operations fit one tile of k
+// qubits; cut after every site (cut_after_sites), after the sites flagged in
+// `cut_after` (indexed by site), and after max_sites_per_pass sites or
+// max_ops_per_pass operations.
+std::vector<PassSpec> segment(const Plan& p, bool cut_after_sites, int max_sites_per_pass, int max_ops_per_pass,
+                              const std::vector<char>* cut_after = nullptr);
 
 // ------------------------------------------------------------------- handle
 struct Engine;     // device-side state (engine.cu)
@@ -112,6 +117,11 @@ struct Handle {
     SetsState* sets = nullptr;
     bool profiling = false;
     nqs_kernel_stats stats[5] = {};
+    // execution options (nqs_set_option): 0 = automatic
+    int opt_spacing = 0;           // sites per checkpoint block
+    int opt_rb_multi = 0;          // register qubits of multi-state sweeps (3 or 4)
+    int opt_max_ops = 0;           // operations per pass (segmentation)
+    int opt_max_sites = 0;         // sites per pass (segmentation)
 };
 
 // engine entry points (engine.cu)
@@ -132,6 +142,8 @@ int pair_training_data(const Handle& h, const float* feats, const double* W2, fl
 int is_estimate(Handle& h, Mlp* mlp, int level, unsigned long long samples, double alpha, unsigned long long seed,
                 const float* feats, const double* W1, nqs_is_result* out, void* stream);
 void engine_destroy(Handle& h);
+void engine_invalidate(Handle& h);     // rebuild the schedule at the next call
+int engine_spacing(const Handle& h, int* n_states);
 uint64_t engine_workspace_bytes(const Handle& h);
 uint64_t engine_upload_bytes(const Handle& h);
 uint64_t engine_launches_per_call(const Handle& h);

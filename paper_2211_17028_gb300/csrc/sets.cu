@@ -12,10 +12,18 @@
 // lexicographic order so that sets with a common first site share the sweep
 // of w_i, and sets with a common first pair share the sweeps of the nine
 // states, each of which reduces at every third site its sets need.
+//
+// When the 2N checkpoints do not fit in device memory (or the handle's
+// checkpoint-spacing option asks for it), chi is kept only at the first site
+// and phi only at the last site of each block of k sites: chi_{s_1} is
+// recomputed by a forward sweep from its block's first site, and a block's
+// phi by a backward sweep from its last site into a ring of k slots, once
+// for every run of reductions that falls in the block.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstring>
+#include <iterator>
 #include <map>
 #include <vector>
 
@@ -31,9 +39,19 @@ struct SetsState {
     size_t aux_bytes = 0;
     void* call = nullptr;
     size_t call_bytes = 0;
-    std::vector<float2*> phi, chi;
+    std::vector<float2*> phi, chi;    // spaced: boundaries per block (phi at block-last, chi at block-first sites)
+    std::vector<float2*> ring;        // spaced: recomputed phi of one block
+    int spacing = 0;                  // sites per checkpoint block (0: every site)
     float2* main = nullptr;
     float2* scratch = nullptr;
+    float2* work = nullptr;           // spaced: recomputed chi
+    float2* work_mat = nullptr;       // spaced: backward recomputation state
+    float2** phi_bd_tab = nullptr;    // spaced: site -> phi boundary of its block
+    std::vector<PassSpec> segs;       // spaced: passes cut after every block-last site
+    std::vector<DevOp> mat_ops;       // spaced: backward ops saving phi at every site, per pass of segs
+    std::vector<std::pair<int, int>> mat_pass;   // (first op in mat_ops, count) per pass, reversed order
+    std::vector<int> mat_seg;         // segment index of each entry of mat_pass
+    std::vector<int> mat_block;       // block of each entry of mat_pass
     float2* g1[3] = {};
     float2* g2[9] = {};
     float2** phi_tab = nullptr;
@@ -261,7 +279,7 @@ int upload_and_run(Handle& h, SetsState& S, Prog& G, size_t extra_bytes, void** 
         if (l.kind == L_PASS) {
             l.args.ops = (const DevOp*)(base + o_ops) + l.op_index;
             l.args.prog = l.rt ? (const uint4*)(base + o_prog) + l.prog_index : nullptr;
-            l.args.ckpt = S.phi_tab;
+            l.args.ckpt = l.bd_table ? S.phi_bd_tab : S.phi_tab;
             l.args.ckpt_fwd = S.chi_tab;
             l.args.partials = E.partials;
             l.args.err = S.err;
@@ -303,26 +321,61 @@ int engine_prepare_sets(Handle& h, const nqs_state* psi, const nqs_state* v, voi
     if (cudaGetDevice(&dev) != cudaSuccess) return NQS_ERR_CUDA;
     cudaDeviceGetAttribute(&S.sm_count, cudaDevAttrMultiProcessorCount, dev);
     const size_t dim = (size_t)1 << plan.n;
-    const size_t n_states = 2 * (size_t)N + 2 + 3 + 9;
-    S.buf_bytes = n_states * dim * sizeof(float2);
-    S.buf = dev_alloc(S.buf_bytes, stream);
+    const size_t sbytes = dim * sizeof(float2);
+    // every site, else blocks of k sites: boundaries 2 ceil(N/k), ring k, five work states, 12 group states
+    auto spaced_states = [&](int k) { return 2 * (size_t)((N + k - 1) / k) + (size_t)k + 5 + 12; };
+    int k = (h.opt_spacing > 0 && h.opt_spacing < N) ? h.opt_spacing : 0;
+    if (k == 0) {
+        S.buf_bytes = (2 * (size_t)N + 2 + 3 + 9) * sbytes;
+        S.buf = dev_alloc(S.buf_bytes, stream);
+        if (!S.buf && h.opt_spacing == 0 && N > 1) {
+            k = 1;
+            for (int c = 2; c < N; ++c)
+                if (spaced_states(c) < spaced_states(k)) k = c;
+        }
+    }
+    if (k > 0) {
+        S.buf_bytes = spaced_states(k) * sbytes;
+        S.buf = dev_alloc(S.buf_bytes, stream);
+    }
     if (!S.buf) {
         S.buf_bytes = 0;
         sets_destroy(h);
         return NQS_ERR_NOMEM;
     }
+    S.spacing = k;
     float2* b = (float2*)S.buf;
     size_t next = 0;
-    for (int s = 0; s < N; ++s) S.phi.push_back(b + (next++) * dim);
-    for (int s = 0; s < N; ++s) S.chi.push_back(b + (next++) * dim);
+    const int nslots = k ? (N + k - 1) / k : N;
+    for (int s = 0; s < nslots; ++s) S.phi.push_back(b + (next++) * dim);
+    for (int s = 0; s < nslots; ++s) S.chi.push_back(b + (next++) * dim);
+    for (int j = 0; j < k; ++j) S.ring.push_back(b + (next++) * dim);
     S.main = b + (next++) * dim;
     S.scratch = b + (next++) * dim;
+    if (k) {
+        S.work = b + (next++) * dim;
+        S.work_mat = b + (next++) * dim;
+        next++;   // spare (keeps the count of spaced_states)
+    }
     for (int i = 0; i < 3; ++i) S.g1[i] = b + (next++) * dim;
     for (int i = 0; i < 9; ++i) S.g2[i] = b + (next++) * dim;
 
-    // matrices: forward factors for every op (and adjoints for the backward run)
+    // matrices: forward factors for every op (and adjoints for the backward runs)
+    std::vector<char> block_last, block_first;
+    if (k) {
+        block_last.assign(N, 0);
+        block_first.assign(N, 0);
+        for (int s = 0; s < N; ++s) {
+            block_last[s] = ((s + 1) % k == 0) || s == N - 1;
+            block_first[s] = s % k == 0;
+        }
+        S.segs = segment(plan, false, h.opt_max_sites > 0 ? h.opt_max_sites : 4,
+                         h.opt_max_ops > 0 ? h.opt_max_ops : 96, &block_last);
+    }
+    const std::vector<PassSpec>& bsegs = k ? S.segs : plan.free_passes;
     std::vector<DevOp> run_ops;
-    Run run_bwd = make_run(plan, plan.free_passes, RT_BWD, false, false, false, h.factors, S.tab, run_ops);
+    Run run_bwd = make_run(plan, bsegs, RT_BWD, false, false, false, h.factors, S.tab, run_ops,
+                           k ? &block_last : nullptr);
     Run run_fwd = make_run(plan, plan.free_passes, RT_FWD, false, false, false, h.factors, S.tab, run_ops);
     S.fwd_mat.assign(plan.ops.size(), -1);
     for (const RunPass& rp : run_fwd.passes)
@@ -330,13 +383,32 @@ int engine_prepare_sets(Handle& h, const nqs_state* psi, const nqs_state* v, voi
     Run run_ideal;
     if (v->kind == NQS_STATE_IDEAL) run_ideal = make_run(plan, plan.free_passes, RT_IDEAL, false, false, false, h.factors,
                                                          S.tab, run_ops);
+    if (k) {
+        // per-block recomputation of phi (saves at every site), kept for evaluation calls
+        Run run_mat = make_run(plan, S.segs, RT_BWD, false, false, false, h.factors, S.tab, S.mat_ops);
+        const int nb = (N + k - 1) / k;
+        for (size_t p = 0; p < run_mat.passes.size(); ++p) {
+            const RunPass& rp = run_mat.passes[p];
+            int blk = nb;
+            if (!rp.lin.empty())
+                for (int c = 0; c < nb; ++c)
+                    if (rp.lin[0] <= plan.site_pos[std::min(N, (c + 1) * k) - 1]) {
+                        blk = c;
+                        break;
+                    }
+            S.mat_pass.push_back({rp.op_off, rp.n_ops});
+            S.mat_seg.push_back((int)(run_mat.passes.size() - 1 - p));
+            S.mat_block.push_back(blk);
+        }
+    }
 
     // aux: checkpoint tables, factor table (complex128), status word, matrix table
     const size_t o_phi = 0, o_chi = align256(N * sizeof(float2*));
     const size_t o_kmat = align256(o_chi + N * sizeof(float2*));
     const size_t o_err = align256(o_kmat + (size_t)N * 32 * sizeof(double));
     const size_t o_mats = align256(o_err + sizeof(int));
-    S.aux_bytes = align256(o_mats + S.tab.mats.size() * sizeof(float2) + 1);
+    const size_t o_bd = align256(o_mats + S.tab.mats.size() * sizeof(float2) + 1);
+    S.aux_bytes = align256(o_bd + N * sizeof(float2*));
     S.aux = dev_alloc(S.aux_bytes, stream);
     if (!S.aux) {
         S.aux_bytes = 0;
@@ -348,6 +420,7 @@ int engine_prepare_sets(Handle& h, const nqs_state* psi, const nqs_state* v, voi
     S.chi_tab = (float2**)(ab + o_chi);
     S.kmats = (double*)(ab + o_kmat);
     S.err = (int*)(ab + o_err);
+    S.phi_bd_tab = (float2**)(ab + o_bd);
     float2* mats_dev = (float2*)(ab + o_mats);
     std::vector<double> kh((size_t)N * 32);
     for (int s = 0; s < N; ++s)
@@ -356,12 +429,19 @@ int engine_prepare_sets(Handle& h, const nqs_state* psi, const nqs_state* v, voi
                 kh[s * 32 + i * 8 + 2 * e] = h.factors[s].K[i][e].real();
                 kh[s * 32 + i * 8 + 2 * e + 1] = h.factors[s].K[i][e].imag();
             }
+    std::vector<float2*> phi_t(N), chi_t(N), bd_t(N);
+    for (int s = 0; s < N; ++s) {
+        phi_t[s] = k ? S.ring[s % k] : S.phi[s];
+        chi_t[s] = k ? S.chi[s / k] : S.chi[s];
+        bd_t[s] = k ? S.phi[s / k] : S.phi[s];
+    }
     int rc = NQS_OK;
     auto up = [&](void* dst, const void* src, size_t bytes) {
         if (bytes && rc == NQS_OK) rc = cuda_err(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
     };
-    up(S.phi_tab, S.phi.data(), N * sizeof(float2*));
-    up(S.chi_tab, S.chi.data(), N * sizeof(float2*));
+    up(S.phi_tab, phi_t.data(), N * sizeof(float2*));
+    up(S.chi_tab, chi_t.data(), N * sizeof(float2*));
+    up(S.phi_bd_tab, bd_t.data(), N * sizeof(float2*));
     up(S.kmats, kh.data(), kh.size() * sizeof(double));
     up(mats_dev, S.tab.mats.data(), S.tab.mats.size() * sizeof(float2));
     if (rc == NQS_OK) rc = cuda_err(cudaMemsetAsync(S.err, 0, sizeof(int), st));
@@ -375,16 +455,19 @@ int engine_prepare_sets(Handle& h, const nqs_state* psi, const nqs_state* v, voi
     Prog G;
     const float2* in1[1];
     float2* out1[1];
-    auto run_passes = [&](const Run& run, const float2* first_in, bool bwd, bool save_fwd) {
+    auto run_passes = [&](const Run& run, const std::vector<PassSpec>& segs, const float2* first_in, bool bwd,
+                          bool save_fwd) {
         for (size_t p = 0; p < run.passes.size(); ++p) {
             const RunPass& rp = run.passes[p];
             std::vector<DevOp> ops(run_ops.begin() + rp.op_off, run_ops.begin() + rp.op_off + rp.n_ops);
             for (DevOp& d : ops)
-                if (d.type == OP_SITE && save_fwd) d.flags = FL_APPLY | FL_SAVE_FWD | (d.flags & FL_KDIAG);
+                if (d.type == OP_SITE && save_fwd)
+                    d.flags = FL_APPLY | ((!k || block_first[d.site]) ? FL_SAVE_FWD : 0) | (d.flags & FL_KDIAG);
             in1[0] = (p == 0 && first_in) ? first_in : S.main;
             out1[0] = S.main;
-            const PassSpec& ps = plan.free_passes[bwd ? run.passes.size() - 1 - p : p];
+            const PassSpec& ps = segs[bwd ? run.passes.size() - 1 - p : p];
             add_launch(G, plan, S, ps, 1, ops, in1, out1, nullptr, 0);
+            if (bwd) G.L.back().bd_table = true;
         }
     };
     auto fill = [&](const nqs_state* st8, const float2*& ext) {
@@ -402,14 +485,14 @@ int engine_prepare_sets(Handle& h, const nqs_state* psi, const nqs_state* v, voi
     const float2* ext = nullptr;
     if (v->kind == NQS_STATE_IDEAL) {
         fill(psi, ext);
-        run_passes(run_ideal, ext, false, false);
+        run_passes(run_ideal, plan.free_passes, ext, false, false);
         ext = nullptr;
     } else {
         fill(v, ext);
     }
-    run_passes(run_bwd, ext, true, false);
+    run_passes(run_bwd, bsegs, ext, true, false);
     fill(psi, ext);
-    run_passes(run_fwd, ext, false, true);
+    run_passes(run_fwd, plan.free_passes, ext, false, true);
     // the matrices of the device table: programs index their own copies, the
     // shared-memory tile kernel reads the table
     for (Launch& l : G.L)
@@ -420,7 +503,6 @@ int engine_prepare_sets(Handle& h, const nqs_state* psi, const nqs_state* v, voi
         sets_destroy(h);
         return rc;
     }
-    // keep the device matrix table for later tile-kernel launches
     S.ready = true;
     return NQS_OK;
 }
@@ -451,17 +533,70 @@ int engine_eval_sets(Handle& h, int k, const int* sets, size_t m, double* W_out,
         return std::lexicographical_compare(sets + x * k, sets + x * k + k, sets + y * k, sets + y * k + k);
     });
     auto at = [&](size_t r, int c) { return sets[order[r] * k + c]; };
+    const int K = S.spacing;
+    // spaced checkpoints: phi of block c into the ring (once per run of reductions in it)
+    int ring_block = -1;
+    auto materialize = [&](int c) {
+        if (!K || ring_block == c) return;
+        bool first_in = true;
+        for (size_t p = 0; p < S.mat_pass.size(); ++p) {
+            if (S.mat_block[p] != c) continue;
+            std::vector<DevOp> ops(S.mat_ops.begin() + S.mat_pass[p].first,
+                                   S.mat_ops.begin() + S.mat_pass[p].first + S.mat_pass[p].second);
+            const float2* in[1] = {first_in ? S.phi[c] : S.work_mat};
+            float2* out[1] = {S.work_mat};
+            add_launch(G, plan, S, S.segs[S.mat_seg[p]], 1, ops, in, out, nullptr, 0);
+            first_in = false;
+        }
+        ring_block = c;
+    };
+    auto phi_of = [&](int t) { return K ? S.ring[t % K] : S.phi[t]; };
+    // chi_{s1}: stored, or swept forward from the first site of its block
+    auto chi_of = [&](int s1) -> const float2* {
+        if (!K) return S.chi[s1];
+        const int first = (s1 / K) * K;
+        if (s1 == first) return S.chi[s1 / K];
+        Launch c;
+        c.kind = L_COPY;
+        c.dst = S.work;
+        c.src = S.chi[s1 / K];
+        G.L.push_back(c);
+        float2* w[1] = {S.work};
+        sweep_range(G, h, S, plan.site_pos[first] - 1, plan.site_pos[s1] - 1, [](int) { return FL_APPLY; }, 1, w,
+                    nullptr, 0, [](int, int, int) { return -1ll; });
+        return S.work;
+    };
+    // sweep `states` from linear op `from` through the reduction sites of
+    // `slots` (site -> value slot base), one checkpoint block at a time
+    auto reduce_through = [&](int from, const std::map<int, long long>& slots, int nst, float2* const* states,
+                              int mult) {
+        int pos = from;
+        for (auto it = slots.begin(); it != slots.end();) {
+            const int blk = K ? it->first / K : 0;
+            auto end = it;
+            while (end != slots.end() && (!K || end->first / K == blk)) ++end;
+            materialize(blk);
+            const int last = std::prev(end)->first;
+            sweep_range(G, h, S, pos, plan.site_pos[last],
+                        [&](int t) { return FL_APPLY | (slots.count(t) ? FL_REDUCE : 0); }, nst, states, nullptr, 0,
+                        [&](int t, int st, int f) { return slots.at(t) + st * mult + f; });
+            pos = plan.site_pos[last];
+            it = end;
+        }
+    };
     for (size_t i = 0; i < m;) {
         const int s1 = at(i, 0);
         size_t i1 = i;
         while (i1 < m && at(i1, 0) == s1) ++i1;
         if (k == 1) {
+            const float2* chi = chi_of(s1);
+            materialize(K ? s1 / K : 0);
             for (size_t r = i; r < i1; ++r) {
                 const long long base = (long long)order[r] * 27;
                 Launch l;
                 l.kind = L_REDUCE2;
-                l.src = S.phi[s1];
-                l.dst = S.chi[s1];
+                l.src = phi_of(s1);
+                l.dst = const_cast<float2*>(chi);   // read only
                 l.bits = (unsigned long long)h.circ.noises[s1].qubit;
                 const long long npairs = 1ll << (plan.n - 1);
                 l.grid = (int)std::max<long long>(
@@ -479,16 +614,14 @@ int engine_eval_sets(Handle& h, int k, const int* sets, size_t m, double* W_out,
         const PassSpec& ps1 = plan.free_passes[pass_of(plan, p1)];
         {
             auto ops = emit_range(plan, S, ps1, p1, p1 + 1, [&](int) { return FL_SPAWN; }, h.factors);
-            const float2* in[1] = {S.chi[s1]};
+            const float2* in[1] = {chi_of(s1)};
             float2* out[1] = {S.scratch};
             add_launch(G, plan, S, ps1, 1, ops, in, out, S.g1, 3);
         }
         if (k == 2) {
             std::map<int, long long> base2;   // second site -> value slots of its set
             for (size_t r = i; r < i1; ++r) base2[at(r, 1)] = (long long)order[r] * 27;
-            const int pmax = plan.site_pos[at(i1 - 1, 1)];
-            sweep_range(G, h, S, p1, pmax, [&](int t) { return FL_APPLY | (base2.count(t) ? FL_REDUCE : 0); }, m1, S.g1,
-                        nullptr, 0, [&](int t, int st, int f) { return base2[t] + st * 3 + f; });
+            reduce_through(p1, base2, m1, S.g1, 3);
             i = i1;
             continue;
         }
@@ -503,12 +636,29 @@ int engine_eval_sets(Handle& h, int k, const int* sets, size_t m, double* W_out,
             pos = p2;
             std::map<int, long long> base3;   // third site -> value slots of its set
             for (size_t q = r; q < r2; ++q) base3[at(q, 2)] = (long long)order[q] * 27;
-            const int pmax = plan.site_pos[at(r2 - 1, 2)];
             const int m2 = h.factors[s2].m;
-            for (int g = 0; g < m1; ++g) {
-                float2* grp[3] = {S.g2[3 * g], S.g2[3 * g + 1], S.g2[3 * g + 2]};
-                sweep_range(G, h, S, p2, pmax, [&](int t) { return FL_APPLY | (base3.count(t) ? FL_REDUCE : 0); }, m2,
-                            grp, nullptr, 0, [&](int t, int st, int f) { return base3[t] + g * 9 + st * 3 + f; });
+            if (!K) {
+                for (int g = 0; g < m1; ++g) {
+                    std::map<int, long long> bg = base3;
+                    for (auto& e : bg) e.second += g * 9;
+                    reduce_through(p2, bg, m2, S.g2 + 3 * g, 3);
+                }
+            } else {
+                // one block at a time for all three groups, so each block's phi is recomputed once
+                int gpos[3] = {p2, p2, p2};
+                for (auto it = base3.begin(); it != base3.end();) {
+                    const int blk = it->first / K;
+                    auto end = it;
+                    while (end != base3.end() && end->first / K == blk) ++end;
+                    std::map<int, long long> part(it, end);
+                    for (int g = 0; g < m1; ++g) {
+                        std::map<int, long long> bg = part;
+                        for (auto& e : bg) e.second += g * 9;
+                        reduce_through(gpos[g], bg, m2, S.g2 + 3 * g, 3);
+                        gpos[g] = plan.site_pos[std::prev(end)->first];
+                    }
+                    it = end;
+                }
             }
             r = r2;
         }

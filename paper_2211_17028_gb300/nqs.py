@@ -31,6 +31,10 @@ NQS_STATE_DENSE = 1
 NQS_STATE_IDEAL = 2
 NQS_PREP_PRUNE_ZERO_RANK = 1
 NQS_MAX_LEVEL = 16
+NQS_OPT_CKPT_SPACING = 1
+NQS_OPT_SWEEP_RB = 2
+NQS_OPT_MAX_OPS = 3
+NQS_OPT_MAX_SITES = 4
 
 
 class NqsError(RuntimeError):
@@ -72,7 +76,8 @@ class nqs_info(ctypes.Structure):
     _fields_ = [("n_qubits", ctypes.c_int32), ("n_gates", ctypes.c_int32), ("n_sites", ctypes.c_int32),
                 ("n_ops", ctypes.c_int32), ("n_passes", ctypes.c_int32), ("tile_qubits", ctypes.c_int32),
                 ("workspace_bytes", ctypes.c_uint64), ("upload_bytes", ctypes.c_uint64),
-                ("launches_per_call", ctypes.c_uint64)]
+                ("launches_per_call", ctypes.c_uint64), ("ckpt_spacing", ctypes.c_int32),
+                ("n_states", ctypes.c_int32)]
 
 
 class nqs_kernel_stats(ctypes.Structure):
@@ -105,6 +110,10 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_size_t)]),
     "nqs_truncation_bound": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "nqs_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(nqs_info)]),
+    "nqs_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]),
+    "nqs_get_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
+    "nqs_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(nqs_state), ctypes.POINTER(nqs_state), ctypes.c_int,
+                                    ctypes.c_int, ctypes.POINTER(nqs_result), ctypes.c_void_p]),
     "nqs_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "nqs_get_kernel_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(nqs_kernel_stats)]),
     "nqs_reduced_matrix": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -326,6 +335,24 @@ def nqs_get_info(h):
     info = nqs_info()
     _check(_lib().nqs_get_info(h, ctypes.byref(info)), "nqs_get_info")
     return {f: getattr(info, f) for f, _ in nqs_info._fields_}
+
+
+def nqs_set_option(h, option, value):
+    _check(_lib().nqs_set_option(h, option, int(value)), "nqs_set_option")
+
+
+def nqs_get_option(h, option):
+    v = ctypes.c_int64()
+    _check(_lib().nqs_get_option(h, option, ctypes.byref(v)), "nqs_get_option")
+    return v.value
+
+
+def nqs_autotune(h, psi, v, level, trials=2, stream=None):
+    ps, vs = _as_state(psi), _as_state(v)
+    out = nqs_result()
+    _check(_lib().nqs_autotune(h, ctypes.byref(ps), ctypes.byref(vs), level, trials, ctypes.byref(out),
+                               _stream_ptr(stream)), "nqs_autotune")
+    return out.to_dict()
 
 
 def nqs_set_profiling(h, on):

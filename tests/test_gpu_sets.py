@@ -56,3 +56,26 @@ def test_site_set_argument_errors():
             nqs.nqs_eval_sets(circ.h, np.array(bad))
         assert e.value.code == nqs.NQS_ERR_ARG
     circ.close()
+
+
+@pytest.mark.parametrize("spacing", [1, 2, 3])
+def test_site_set_weights_with_spaced_checkpoints(spacing):
+    """Checkpoints kept every `spacing` sites (chi at block-first, phi at
+    block-last sites, the rest recomputed per call) give the same W(S)."""
+    from paper_2211_17028_gb300 import nqs
+    w = W.random_circuit(75, 13, 60, 7, v_kind="ideal", rate_lo=1e-3, rate_hi=3e-2)
+    ref = oracle_result(w, 3)
+    want = site_sets([r for r, _ in ref["terms"]], [x.real for _, x in ref["terms"]])
+    F = ref["F"].real
+    circ = nqs.NoisyCircuit(W.to_ir_text(w))
+    nqs.nqs_set_option(circ.h, nqs.NQS_OPT_CKPT_SPACING, spacing)
+    nqs.nqs_prepare_sets(circ.h, nqs.basis(w.psi["bits"]), nqs.ideal())
+    N = w.n_noise
+    for k in (1, 2, 3):
+        sets = np.array(list(itertools.combinations(range(N), k)), dtype=np.int32)
+        # shuffled order: the evaluation sorts internally and must map values back
+        perm = np.random.default_rng(k).permutation(len(sets))
+        got = nqs.nqs_eval_sets(circ.h, sets[perm])
+        for s, g in zip(sets[perm], got):
+            assert abs(g - want[tuple(int(x) for x in s)]) <= REL_TOL * abs(F), (spacing, k, s, g)
+    circ.close()
