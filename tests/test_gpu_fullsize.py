@@ -136,3 +136,60 @@ def test_qaoa30_level2_sampled_terms():
     W2 *= rest((0, 1)).real
     assert abs(got[(0, 1)] - W2) <= REL_TOL * F, (got[(0, 1)], W2)
     assert abs(got[(0, 1)] - W2) <= 1e-2 * W2, (got[(0, 1)], W2)
+
+
+def test_n31_level1_needs_spaced_checkpoints():
+    """A 31-qubit circuit (16 GiB states) with 20 depolarizing noises: keeping
+    phi at every site (21 states, 336 GiB) does not fit in HBM, so the engine
+    keeps it every k sites and recomputes the rest.  Checked at full size:
+    T_0 = prod_s |c_s c'_s| (dominant factors are multiples of the identity
+    and v = U|psi>), F = T_0 + T_1, and the level-1 sums of the first two
+    sites against the oracle's FP64 prefix sweep."""
+    import torch
+    from paper_2211_17028_gb300 import nqs
+    torch.cuda.set_device(0)
+    nqs.use_torch_allocator()
+    torch.cuda.empty_cache()
+    w = W.random_circuit(131, 31, 240, 20, noise_kinds=("depol",), v_kind="ideal", rate_lo=1e-3, rate_hi=1e-2)
+    text = W.to_ir_text(w)
+    circ = nqs.NoisyCircuit(text)
+    res = circ.fidelity(nqs.basis(w.psi["bits"]), nqs.ideal(), 1)
+    info = nqs.nqs_get_info(circ.h)
+    recs = nqs.nqs_enumerate_terms(circ.h, 1)
+    vals = circ.term_values()
+    circ.close()
+    torch.cuda.empty_cache()
+    assert res["status"] == 0
+    assert info["ckpt_spacing"] > 0 and info["n_states"] < 21
+    got = site_sets(recs, vals)
+    F = res["F"]
+    assert abs(F - res["T"][0] - res["T"][1]) <= 1e-12 * F
+
+    c = OIR.parse(text)
+    fac = OEX.prepared_factors(c)
+    cu = [_identity_scale(f[1][0]) for f in fac]
+    cv = [_identity_scale(f[2][0]) for f in fac]
+    T0 = np.prod([(a * b).real for a, b in zip(cu, cv)])
+    assert abs(res["T"][0] - T0) <= REL_TOL * F, (res["T"][0], T0)
+    ev = {idx: e for e, (kind, idx) in enumerate(OIR.events(c)) if kind == "noise"}
+    n = c.n
+    chi = np.zeros(1 << n, dtype=np.complex128)
+    chi[w.psi["bits"]] = 1.0
+    pos = 0
+    for s in range(2):
+        csim.apply_ops(n, chi, _gate_ops(c, pos, ev[s]))
+        pos = ev[s]
+        q = c.noises[s][1]
+        W1 = 0.0
+        for i in (1, 2, 3):
+            x = chi.copy()
+            csim.apply_ops(n, x, _one(q, fac[s][1][i]))
+            a = csim.inner(n, chi, x)
+            x[:] = chi
+            csim.apply_ops(n, x, _one(q, fac[s][2][i].conj()))
+            b = csim.inner(n, chi, x).conjugate()
+            del x
+            W1 += (a * b).real
+        W1 *= np.prod([(cu[u] * cv[u]).real for u in range(len(fac)) if u != s])
+        assert abs(got[(s,)] - W1) <= REL_TOL * F, (s, got[(s,)], W1)
+        assert abs(got[(s,)] - W1) <= 1e-2 * W1 + 1e-12, (s, got[(s,)], W1)
