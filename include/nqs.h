@@ -185,6 +185,29 @@ typedef struct {
 
 int nqs_get_info(nqs_handle h, nqs_info* out);
 
+/* Launch list of the handle's current schedule (the one the last
+ * nqs_fidelity call built), for profiling: one record per launch, in launch
+ * order.  kind: 0 sweep pass, 1 finisher, 2 state fill, 3 state copy,
+ * 4 two-state reduction, 5 level sums.  For sweep passes: states swept
+ * together, register qubits per thread (0: shared-memory tile kernel), phases
+ * of the register-resident program, grid size, operation counts
+ * ops[] = {dense 1-qubit, dense 2-qubit, diagonal 1-qubit, diagonal 2-qubit,
+ * noise sites, site reductions, spawned states, checkpoint saves} and the
+ * algorithmic bytes of the launch (see nqs_kernel_stats).  Call with out =
+ * NULL (or cap too small) to get the count only.  No counterpart in the paper. */
+typedef struct {
+    int32_t kind;
+    int32_t states;
+    int32_t reg_qubits;
+    int32_t phases;
+    int32_t grid;
+    int32_t ops[8];
+    int32_t pad_;
+    double algorithmic_bytes;
+} nqs_launch_info;
+
+int nqs_schedule_launches(nqs_handle h, nqs_launch_info* out, size_t cap, size_t* count);
+
 /* ---- execution options ----------------------------------------------------
  * Choices of this library with no counterpart in the paper; value 0 restores
  * the automatic choice.  A change takes effect at the next call (the schedule

@@ -278,6 +278,12 @@ void resegment(Handle& h) {
 
 }  // namespace
 
+int nqs_schedule_launches(nqs_handle hh, nqs_launch_info* out, size_t cap, size_t* count) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !count) return NQS_ERR_ARG;
+    return engine_launch_list(*h, out, cap, count);
+}
+
 int nqs_set_option(nqs_handle hh, int option, int64_t value) {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h || value < 0) return NQS_ERR_ARG;

@@ -344,6 +344,7 @@ struct Builder {
         int n_red = 0, n_save = 0, n_sp = 0;
         for (int o = start; o < rp.n_ops; ++o) {
             const DevOp& d = dops[rp.op_off + o];
+            if (d.type >= OP_G1 && d.type <= OP_SITE) ++l.op_counts[d.type - OP_G1];
             if (d.type != OP_SITE) continue;
             if (d.flags & FL_REDUCE) ++n_red;
             if (d.flags & FL_SAVE) ++n_save;
@@ -351,6 +352,9 @@ struct Builder {
         }
         b += 8.0 * dim * (n_red + n_save + (double)n_sp * S);
         l.bytes = b;
+        l.op_counts[5] = n_red;
+        l.op_counts[6] = n_sp * S;
+        l.op_counts[7] = n_save;
         L.push_back(l);
     }
 
@@ -1061,6 +1065,27 @@ uint64_t engine_upload_bytes(const Handle& h) { return h.eng ? h.eng->upload_byt
 void engine_invalidate(Handle& h) {
     if (h.eng) h.eng->level = -1;
     engine_batch_forget(&h);
+}
+
+int engine_launch_list(const Handle& h, nqs_launch_info* out, size_t cap, size_t* count) {
+    const size_t n = (h.eng && h.eng->level >= 0) ? h.eng->launches.size() : 0;
+    *count = n;
+    if (!out || cap < n) return NQS_OK;
+    for (size_t i = 0; i < n; ++i) {
+        const Launch& l = h.eng->launches[i];
+        nqs_launch_info& o = out[i];
+        std::memset(&o, 0, sizeof(o));
+        o.kind = (int32_t)l.kind;
+        if (l.kind == L_PASS) {
+            o.states = l.S;
+            o.reg_qubits = l.rt ? l.rb : 0;
+            o.phases = l.rt ? l.args.n_phases : 0;
+            o.grid = l.grid;
+            for (int c = 0; c < 8; ++c) o.ops[c] = l.op_counts[c];
+            o.algorithmic_bytes = l.bytes;
+        }
+    }
+    return NQS_OK;
 }
 
 int engine_spacing(const Handle& h, int* n_states) {

@@ -48,6 +48,7 @@ struct Launch {
     unsigned long long bits = 0;
     double bytes = 0;                // algorithmic bytes (pass kernels)
     bool bd_table = false;           // pass saves through the block-boundary checkpoint table
+    int op_counts[8] = {};           // pass: G1, G2, D1, D2, sites, reductions, spawned states, saves
 };
 
 struct Engine {

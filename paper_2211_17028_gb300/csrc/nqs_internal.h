@@ -144,6 +144,7 @@ int is_estimate(Handle& h, Mlp* mlp, int level, unsigned long long samples, doub
 void engine_destroy(Handle& h);
 void engine_invalidate(Handle& h);     // rebuild the schedule at the next call
 int engine_spacing(const Handle& h, int* n_states);
+int engine_launch_list(const Handle& h, nqs_launch_info* out, size_t cap, size_t* count);
 uint64_t engine_workspace_bytes(const Handle& h);
 uint64_t engine_upload_bytes(const Handle& h);
 uint64_t engine_launches_per_call(const Handle& h);

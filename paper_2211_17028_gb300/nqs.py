@@ -80,6 +80,12 @@ class nqs_info(ctypes.Structure):
                 ("n_states", ctypes.c_int32)]
 
 
+class nqs_launch_info(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("states", ctypes.c_int32), ("reg_qubits", ctypes.c_int32),
+                ("phases", ctypes.c_int32), ("grid", ctypes.c_int32), ("ops", ctypes.c_int32 * 8),
+                ("pad_", ctypes.c_int32), ("algorithmic_bytes", ctypes.c_double)]
+
+
 class nqs_kernel_stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
                 ("algorithmic_bytes", ctypes.c_double)]
@@ -111,6 +117,8 @@ _SIGS = {
     "nqs_truncation_bound": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "nqs_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(nqs_info)]),
     "nqs_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]),
+    "nqs_schedule_launches": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                             ctypes.POINTER(ctypes.c_size_t)]),
     "nqs_get_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
     "nqs_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(nqs_state), ctypes.POINTER(nqs_state), ctypes.c_int,
                                     ctypes.c_int, ctypes.POINTER(nqs_result), ctypes.c_void_p]),
@@ -335,6 +343,26 @@ def nqs_get_info(h):
     info = nqs_info()
     _check(_lib().nqs_get_info(h, ctypes.byref(info)), "nqs_get_info")
     return {f: getattr(info, f) for f, _ in nqs_info._fields_}
+
+
+LAUNCH_KINDS = ("pass", "finish", "fill", "copy", "reduce2", "sum")
+OP_COUNT_NAMES = ("g1", "g2", "d1", "d2", "sites", "reductions", "spawned", "saves")
+
+
+def nqs_schedule_launches(h):
+    """Launch list of the current schedule as a list of dicts."""
+    cnt = ctypes.c_size_t()
+    _check(_lib().nqs_schedule_launches(h, None, 0, ctypes.byref(cnt)), "nqs_schedule_launches")
+    buf = (nqs_launch_info * max(1, cnt.value))()
+    _check(_lib().nqs_schedule_launches(h, buf, cnt.value, ctypes.byref(cnt)), "nqs_schedule_launches")
+    out = []
+    for i in range(cnt.value):
+        r = buf[i]
+        d = {"kind": LAUNCH_KINDS[r.kind], "states": r.states, "reg_qubits": r.reg_qubits, "phases": r.phases,
+             "grid": r.grid, "algorithmic_bytes": r.algorithmic_bytes}
+        d.update({k: r.ops[j] for j, k in enumerate(OP_COUNT_NAMES)})
+        out.append(d)
+    return out
 
 
 def nqs_set_option(h, option, value):
