@@ -84,8 +84,26 @@ __device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
 }
 
 // ---- dense operations on register qubits -----------------------------------
+// Packed FP32x2 form of a complex product on interleaved (re, im) pairs:
+//   m a = (m.x, m.x) * (a.x, a.y) + (-m.y, m.y) * (a.y, a.x)
+// so one output of the 2x2 gate is four packed operations (multi-state passes).
 template <int I, int S, int E>
 __device__ __forceinline__ void g1_reg(float2 (&x)[S][E], float2 m0, float2 m1, float2 m2, float2 m3) {
+    if constexpr (S == 1) {   // the 16-amplitude single-state layout has no registers to spare
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            if (r & (1 << I)) continue;
+            const int r1 = r | (1 << I);
+            const float2 a = x[0][r], b = x[0][r1];
+            x[0][r] = cfma(m0, a, cmul(m1, b));
+            x[0][r1] = cfma(m2, a, cmul(m3, b));
+        }
+        return;
+    }
+    const float2 p0 = make_float2(m0.x, m0.x), q0 = make_float2(-m0.y, m0.y);
+    const float2 p1 = make_float2(m1.x, m1.x), q1 = make_float2(-m1.y, m1.y);
+    const float2 p2 = make_float2(m2.x, m2.x), q2 = make_float2(-m2.y, m2.y);
+    const float2 p3 = make_float2(m3.x, m3.x), q3 = make_float2(-m3.y, m3.y);
 #pragma unroll
     for (int r = 0; r < E; ++r) {
         if (r & (1 << I)) continue;
@@ -93,8 +111,17 @@ __device__ __forceinline__ void g1_reg(float2 (&x)[S][E], float2 m0, float2 m1, 
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             const float2 a = x[s][r], b = x[s][r1];
-            x[s][r] = cfma(m0, a, cmul(m1, b));
-            x[s][r1] = cfma(m2, a, cmul(m3, b));
+            const float2 as = make_float2(a.y, a.x), bs = make_float2(b.y, b.x);
+            float2 y0 = __fmul2_rn(p0, a);
+            y0 = __ffma2_rn(q0, as, y0);
+            y0 = __ffma2_rn(p1, b, y0);
+            y0 = __ffma2_rn(q1, bs, y0);
+            float2 y1 = __fmul2_rn(p2, a);
+            y1 = __ffma2_rn(q2, as, y1);
+            y1 = __ffma2_rn(p3, b, y1);
+            y1 = __ffma2_rn(q3, bs, y1);
+            x[s][r] = y0;
+            x[s][r1] = y1;
         }
     }
 }
