@@ -13,9 +13,12 @@ at sites s < t reduce to
 
 (chi_s = gates before site s applied to psi, W = gates between s and t), so
 the oracle needs only the prefix of the circuit up to the sampled sites,
-swept in FP64 by its C state-vector code.  Checked: T_0, the level-1 sums of
-the first three sites and the level-2 sum of the first pair, each within
-1e-5 F and, as these sums are far below F, within 1% of itself; T_1 equals the sum of all level-1 site sums; F = T_0 + T_1 + T_2."""
+swept in FP64 by its C state-vector code (one forward pass through the whole
+circuit, at 16 GiB per FP64 state).  Checked: T_0, the level-1 sums of all 20
+sites, and the level-2 sums of every pair of sites at most 14 operations
+apart (9 pairs: the oracle sweeps the gap between them for each factor),
+each within 1e-5 F and, as these sums are far below F, within 1% of itself;
+T_1 equals the sum of all level-1 site sums; F = T_0 + T_1 + T_2."""
 
 import numpy as np
 import pytest
@@ -88,11 +91,16 @@ def test_qaoa30_level2_sampled_terms():
     assert abs(res["T"][0] - T0.real) <= REL_TOL * F, (res["T"][0], T0)
 
     n = c.n
+    N = len(fac)
+    # level-2 pairs the oracle can afford at n = 30: sites at most 14 events apart
+    pairs = [(s, t) for s in range(N) for t in range(s + 1, N) if ev[t] - ev[s] <= 14]
+    assert len(pairs) >= 8
+    firsts = {s for s, _ in pairs}
     chi = np.zeros(1 << n, dtype=np.complex128)
     chi[0] = 1.0
     pos = 0
-    states = {}
-    for s in range(3):
+    saved = {}
+    for s in range(N):
         csim.apply_ops(n, chi, _gate_ops(c, pos, ev[s]))
         pos = ev[s]
         q = c.noises[s][1]
@@ -110,32 +118,38 @@ def test_qaoa30_level2_sampled_terms():
         assert abs(got[(s,)] - W1) <= REL_TOL * F, (s, got[(s,)], W1)
         # the sums are far below F here: also hold each to 1% of itself
         assert abs(got[(s,)] - W1) <= 1e-2 * W1, (s, got[(s,)], W1)
-        if s < 2:
-            states[s] = chi.copy()
+        # level 2: every close pair ending here, from the saved chi of its first site
+        for (s0, t) in pairs:
+            if t != s:
+                continue
+            q0 = c.noises[s0][1]
+            between = _gate_ops(c, ev[s0], ev[t])
+            W2 = 0.0
+            for i in (1, 2, 3):
+                amps = {}
+                for side in (1, 2):
+                    y = saved[s0].copy()
+                    m0 = fac[s0][side][i] if side == 1 else fac[s0][side][i].conj()
+                    csim.apply_ops(n, y, _one(q0, m0))
+                    csim.apply_ops(n, y, between)
+                    for j in (1, 2, 3):
+                        z = y.copy()
+                        m1 = fac[t][side][j] if side == 1 else fac[t][side][j].conj()
+                        csim.apply_ops(n, z, _one(q, m1))
+                        amps[(side, j)] = csim.inner(n, chi, z)
+                        del z
+                    del y
+                for j in (1, 2, 3):
+                    W2 += (amps[(1, j)] * amps[(2, j)].conjugate()).real
+            W2 *= rest((s0, t)).real
+            assert abs(got[(s0, t)] - W2) <= REL_TOL * F, ((s0, t), got[(s0, t)], W2)
+            assert abs(got[(s0, t)] - W2) <= 1e-2 * W2, ((s0, t), got[(s0, t)], W2)
+        if s in firsts:
+            saved[s] = chi.copy()
+        for s0 in list(saved):
+            if all(t <= s for (a0, t) in pairs if a0 == s0):
+                del saved[s0]
     del chi
-    # level 2, sites (0, 1)
-    q0, q1 = c.noises[0][1], c.noises[1][1]
-    between = _gate_ops(c, ev[0], ev[1])
-    W2 = 0.0
-    for i in (1, 2, 3):
-        amps = {}
-        for side in (1, 2):
-            y = states[0].copy()
-            m0 = fac[0][side][i] if side == 1 else fac[0][side][i].conj()
-            csim.apply_ops(n, y, _one(q0, m0))
-            csim.apply_ops(n, y, between)
-            for j in (1, 2, 3):
-                z = y.copy()
-                m1 = fac[1][side][j] if side == 1 else fac[1][side][j].conj()
-                csim.apply_ops(n, z, _one(q1, m1))
-                amps[(side, j)] = csim.inner(n, states[1], z)
-                del z
-            del y
-        for j in (1, 2, 3):
-            W2 += (amps[(1, j)] * amps[(2, j)].conjugate()).real
-    W2 *= rest((0, 1)).real
-    assert abs(got[(0, 1)] - W2) <= REL_TOL * F, (got[(0, 1)], W2)
-    assert abs(got[(0, 1)] - W2) <= 1e-2 * W2, (got[(0, 1)], W2)
 
 
 def test_n31_level1_needs_spaced_checkpoints():
