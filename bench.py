@@ -476,6 +476,11 @@ def run_twin_is(args):
     clocks.start()
     full, t_full = timed(lambda: circ.fidelity(psi, v, 3))
     T3 = full["T"][3]
+    vals3 = circ.term_values()
+    o3 = 1 + 3 * N + 9 * (N * (N - 1) // 2)
+    W3 = vals3[o3:].reshape(-1, 27).sum(1)   # exact weight of every level-3 site set, canonical order
+    del vals3
+    proposals = {}
 
     def learned(use_net):
         r2 = circ.fidelity(psi, v, 2)
@@ -494,7 +499,9 @@ def run_twin_is(args):
             nqs.nqs_mlp_train(m, torch.tensor(X, device="cuda"), torch.tensor(y, device="cuda"), batch=1024,
                               steps=2000, lr=2e-3, seed=1)
         nqs.nqs_prepare_sets(circ.h, psi, v)
-        est = nqs.nqs_is_estimate(circ.h, m, 3, samples, 0.3 if use_net else 1.0, 99, feats, W1)
+        alpha = 0.3 if use_net else 1.0
+        est = nqs.nqs_is_estimate(circ.h, m, 3, samples, alpha, 99, feats, W1)
+        proposals[use_net] = nqs.nqs_is_proposal(circ.h, m, 3, alpha, feats, W1)
         if m is not None:
             nqs.nqs_mlp_destroy(m)
         return r2, est
@@ -503,6 +510,16 @@ def run_twin_is(args):
     (_, est_u), t_u = timed(lambda: learned(False))
     clk = clocks.stop()
     n3 = math.comb(N, 3) * 27
+    target = 1e-7   # |dF| target on T_3 (level 2 alone already meets 1e-6 here)
+
+    def exact(use_net, t_total, est):
+        q = proposals[use_net]
+        relvar = float((W3 ** 2 / q).sum() / T3 ** 2 - 1.0)
+        draws = relvar * T3 ** 2 / target ** 2
+        t_draw = t_total / samples   # upper bound: includes level 2, training and checkpoints
+        return {"relative_variance_per_draw": relvar,
+                "expected_stderr_at_samples": math.sqrt(relvar / samples) * T3,
+                "draws_for_stderr_1e-7": draws, "est_s_for_stderr_1e-7": draws * t_draw}
     F_full = full["F"]
     line = {"metric": METRIC, "value": n3 / t_l, "unit": "level-3 terms/s (covered)", "n_gpus": 1, "steps": 1,
             "warmup": 0, "ms_per_step": 1000.0 * t_l, "higher_is_better": True, "scaling": "weak",
@@ -516,7 +533,8 @@ def run_twin_is(args):
                         "distinct_sets": est_l["distinct"], "abs_dF_vs_level3": abs(r2["F"] + est_l["estimate"] - F_full)},
             "uniform": {"s": t_u, "T3": est_u["estimate"], "stderr": est_u["stderr_"],
                         "abs_dF_vs_level3": abs(r2["F"] + est_u["estimate"] - F_full)},
-            "stderr_ratio_uniform_over_learned": est_u["stderr_"] / est_l["stderr_"] if est_l["stderr_"] else None,
+            "exact_variance": {"learned": exact(True, t_l, est_l), "uniform": exact(False, t_u, est_u),
+                               "note": "sum W^2/q - T^2 over all 1,313,400 sets, W from the full enumeration"},
             "clocks": clk}
     print(json.dumps(line))
     circ.close()

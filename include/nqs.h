@@ -377,6 +377,15 @@ typedef struct {
 int nqs_is_estimate(nqs_handle h, nqs_mlp mlp, int level, uint64_t samples, double alpha, uint64_t seed,
                     const float* feats, const double* W1, nqs_is_result* out, void* stream);
 
+/* The proposal nqs_is_estimate draws from: q[i] for every site set of the
+ * level in canonical (lexicographic) order, summing to 1 (same arguments as
+ * nqs_is_estimate).  With the exact per-set weights W (from a full
+ * enumeration) the estimator's variance per draw is sum W^2/q - T^2, which
+ * judges a proposal without sampling noise.  q_out: host, cap doubles; call
+ * with q_out = NULL to get the count.  No counterpart in the paper. */
+int nqs_is_proposal(nqs_handle h, nqs_mlp mlp, int level, double alpha, const float* feats, const double* W1,
+                    double* q_out, size_t cap, size_t* count, void* stream);
+
 void nqs_destroy(nqs_handle h);
 const char* nqs_strerror(int code);
 const char* nqs_version(void);

@@ -493,6 +493,14 @@ int nqs_is_estimate(nqs_handle hh, nqs_mlp mlp, int level, uint64_t samples, dou
     return is_estimate(*h, reinterpret_cast<Mlp*>(mlp), level, samples, alpha, seed, feats, W1, out, stream);
 }
 
+int nqs_is_proposal(nqs_handle hh, nqs_mlp mlp, int level, double alpha, const float* feats, const double* W1,
+                    double* q_out, size_t cap, size_t* count, void* stream) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !count || !W1 || (mlp && !feats)) return NQS_ERR_ARG;
+    if (!h->prepared) return NQS_ERR_ORDER;
+    return is_proposal_values(*h, reinterpret_cast<Mlp*>(mlp), level, alpha, feats, W1, q_out, cap, count, stream);
+}
+
 void nqs_destroy(nqs_handle hh) {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h) return;

@@ -84,10 +84,13 @@ int pair_training_data(const Handle& h, const float* feats, const double* W2, fl
     return NQS_OK;
 }
 
-int is_estimate(Handle& h, Mlp* mlp, int level, unsigned long long samples, double alpha, unsigned long long seed,
-                const float* feats, const double* W1, nqs_is_result* out, void* stream) {
+// The proposal q over all site sets of the level, in canonical (lexicographic)
+// order, with the sets themselves; alpha becomes 1 without a network (or
+// when the network's weights sum to nothing).
+int is_proposal(Handle& h, Mlp* mlp, int level, double& alpha, const float* feats, const double* W1,
+                std::vector<int>& sets, std::vector<double>& q, void* stream) {
     const int N = (int)h.factors.size();
-    if (level < 2 || level > 3 || N < level || samples < 2 || !(alpha >= 0.0 && alpha <= 1.0)) return NQS_ERR_ARG;
+    if (level < 2 || level > 3 || N < level || !(alpha >= 0.0 && alpha <= 1.0)) return NQS_ERR_ARG;
     if (!mlp) alpha = 1.0;
     if (mlp && mlp_n_in(mlp) != 8) return NQS_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
@@ -126,7 +129,7 @@ int is_estimate(Handle& h, Mlp* mlp, int level, unsigned long long samples, doub
             for (int t = s + 1; t < N; ++t, ++r) g[(size_t)s * N + t] = g[(size_t)t * N + s] = ys[r];
     }
     // proposal over all site sets, canonical (lexicographic) order
-    std::vector<int> sets;
+    sets.clear();
     std::vector<double> w;
     const bool learned = mlp && alpha < 1.0;
     std::vector<double> w2(g.size());
@@ -155,7 +158,7 @@ int is_estimate(Handle& h, Mlp* mlp, int level, unsigned long long samples, doub
             }
         }
     const size_t n_sets = w.size();
-    std::vector<double> q(n_sets);
+    q.assign(n_sets, 0.0);
     {
         double z = 0.0;
         for (double x : w) z += x;
@@ -163,6 +166,17 @@ int is_estimate(Handle& h, Mlp* mlp, int level, unsigned long long samples, doub
         for (size_t i = 0; i < n_sets; ++i)
             q[i] = (alpha < 1.0 ? (1.0 - alpha) * w[i] / z : 0.0) + alpha / (double)n_sets;
     }
+    return NQS_OK;
+}
+
+int is_estimate(Handle& h, Mlp* mlp, int level, unsigned long long samples, double alpha, unsigned long long seed,
+                const float* feats, const double* W1, nqs_is_result* out, void* stream) {
+    if (samples < 2) return NQS_ERR_ARG;
+    std::vector<int> sets;
+    std::vector<double> q;
+    int rc0 = is_proposal(h, mlp, level, alpha, feats, W1, sets, q, stream);
+    if (rc0) return rc0;
+    const size_t n_sets = q.size();
     std::vector<double> cdf(n_sets);
     {
         double acc = 0.0;
@@ -206,6 +220,17 @@ int is_estimate(Handle& h, Mlp* mlp, int level, unsigned long long samples, doub
     out->n_sets = n_sets;
     out->level = level;
     out->status = NQS_OK;
+    return NQS_OK;
+}
+
+int is_proposal_values(Handle& h, Mlp* mlp, int level, double alpha, const float* feats, const double* W1,
+                       double* q_out, size_t cap, size_t* count, void* stream) {
+    std::vector<int> sets;
+    std::vector<double> q;
+    const int rc = is_proposal(h, mlp, level, alpha, feats, W1, sets, q, stream);
+    if (rc) return rc;
+    *count = q.size();
+    if (q_out && cap >= q.size()) std::copy(q.begin(), q.end(), q_out);
     return NQS_OK;
 }
 

@@ -141,6 +141,8 @@ int pair_training_data(const Handle& h, const float* feats, const double* W2, fl
                        size_t* count);
 int is_estimate(Handle& h, Mlp* mlp, int level, unsigned long long samples, double alpha, unsigned long long seed,
                 const float* feats, const double* W1, nqs_is_result* out, void* stream);
+int is_proposal_values(Handle& h, Mlp* mlp, int level, double alpha, const float* feats, const double* W1,
+                       double* q_out, size_t cap, size_t* count, void* stream);
 void engine_destroy(Handle& h);
 void engine_invalidate(Handle& h);     // rebuild the schedule at the next call
 int engine_spacing(const Handle& h, int* n_states);

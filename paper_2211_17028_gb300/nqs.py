@@ -153,6 +153,9 @@ _SIGS = {
     "nqs_is_estimate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
                                        ctypes.c_double, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.POINTER(nqs_is_result), ctypes.c_void_p]),
+    "nqs_is_proposal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                       ctypes.POINTER(ctypes.c_size_t), ctypes.c_void_p]),
     "nqs_destroy": (None, [ctypes.c_void_p]),
     "nqs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "nqs_version": (ctypes.c_char_p, []),
@@ -515,6 +518,20 @@ def nqs_is_estimate(h, mlp, level, samples, alpha, seed, feats, W1, stream=None)
     _check(_lib().nqs_is_estimate(h, mlp, level, samples, alpha, seed, None if f is None else f.ctypes.data,
                                   w1.ctypes.data, ctypes.byref(out), _stream_ptr(stream)), "nqs_is_estimate")
     return out.to_dict()
+
+
+def nqs_is_proposal(h, mlp, level, alpha, feats, W1, stream=None):
+    """Proposal probabilities over every site set of the level (canonical order)."""
+    import numpy as np
+    f = None if feats is None else np.ascontiguousarray(feats, dtype=np.float32)
+    w1 = np.ascontiguousarray(W1, dtype=np.float64)
+    cnt = ctypes.c_size_t()
+    args = (h, mlp, level, alpha, None if f is None else f.ctypes.data, w1.ctypes.data)
+    _check(_lib().nqs_is_proposal(*args, None, 0, ctypes.byref(cnt), _stream_ptr(stream)), "nqs_is_proposal")
+    q = np.zeros(cnt.value, dtype=np.float64)
+    _check(_lib().nqs_is_proposal(*args, q.ctypes.data, q.size, ctypes.byref(cnt), _stream_ptr(stream)),
+           "nqs_is_proposal")
+    return q
 
 
 def nqs_destroy(h):
