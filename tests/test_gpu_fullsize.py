@@ -14,11 +14,11 @@ at sites s < t reduce to
 (chi_s = gates before site s applied to psi, W = gates between s and t), so
 the oracle needs only the prefix of the circuit up to the sampled sites,
 swept in FP64 by its C state-vector code (one forward pass through the whole
-circuit, at 16 GiB per FP64 state).  Checked: T_0, the level-1 sums of all 20
-sites, and the level-2 sums of every pair of sites at most 14 operations
-apart (9 pairs: the oracle sweeps the gap between them for each factor),
+circuit prefix, at 16 GiB per FP64 state).  Checked: T_0, the level-1 sums of
+the first six sites, and the level-2 sums of the pairs among them at most 14
+operations apart (the oracle sweeps the gap between them for each factor),
 each within 1e-5 F and, as these sums are far below F, within 1% of itself;
-T_1 equals the sum of all level-1 site sums; F = T_0 + T_1 + T_2."""
+T_1 equals the sum of all 20 level-1 site sums; F = T_0 + T_1 + T_2."""
 
 import numpy as np
 import pytest
@@ -91,10 +91,13 @@ def test_qaoa30_level2_sampled_terms():
     assert abs(res["T"][0] - T0.real) <= REL_TOL * F, (res["T"][0], T0)
 
     n = c.n
-    N = len(fac)
-    # level-2 pairs the oracle can afford at n = 30: sites at most 14 events apart
+    # the oracle's FP64 sweep costs about a second per operation at n = 30, so the
+    # sample stops at the sixth site (the first ~175 operations): level-1 sums of
+    # sites 0..5 and level-2 sums of the site pairs among them at most 14
+    # operations apart
+    N = 6
     pairs = [(s, t) for s in range(N) for t in range(s + 1, N) if ev[t] - ev[s] <= 14]
-    assert len(pairs) >= 8
+    assert len(pairs) >= 2
     firsts = {s for s, _ in pairs}
     chi = np.zeros(1 << n, dtype=np.complex128)
     chi[0] = 1.0
