@@ -281,6 +281,26 @@ struct Builder {
 
     Builder(Handle& hh, Engine& ee, int lvl) : h(hh), E(ee), plan(hh.plan), level(lvl) {
         dim = 1ll << plan.n;
+        const int N = (int)hh.factors.size();
+        if (N > 0) {
+            first_site_pos = plan.site_pos[0];
+            last_site_pos = plan.site_pos[lvl == 0 ? 0 : N - 1];
+        }
+    }
+
+    // Sweeps need nothing outside [first site, last reducing site]: the
+    // backward sweep stops once phi of the first site is saved, forward and
+    // branch sweeps once the last site that reduces or spawns is passed.
+    // Passes lying entirely outside that range are skipped.
+    int first_site_pos = -1;
+    int last_site_pos = 1 << 30;
+    bool before_first(const RunPass& rp) const {
+        if (rp.lin.empty()) return false;
+        return *std::max_element(rp.lin.begin(), rp.lin.end()) < first_site_pos;
+    }
+    bool after_last(const RunPass& rp) const {
+        if (rp.lin.empty()) return false;
+        return *std::min_element(rp.lin.begin(), rp.lin.end()) > last_site_pos;
     }
 
     int grid_for(int S, int RB, long long tiles, int prog_words, int n_events) {
@@ -414,6 +434,7 @@ struct Builder {
         const bool can_spawn = depth + 1 < (int)group_bufs.size();
         for (size_t p = pi; p < run.passes.size(); ++p) {
             const RunPass& rp = run.passes[p];
+            if (after_last(rp)) break;
             int st = (p == (size_t)pi) ? start : 0;
             bool spawns = can_spawn && rp.spawn_site >= 0 && rp.lin.size() > 0;
             // a spawn before `st` (partial first pass) does not execute
@@ -517,7 +538,7 @@ struct Builder {
             if (ring_block == c) return;
             bool first_in = true;
             for (size_t p = 0; p < run_mat.passes.size(); ++p) {
-                if (bm[p] != c) continue;
+                if (bm[p] != c || before_first(run_mat.passes[p])) continue;
                 const float2* in[1] = {first_in ? bd[c] : work_buf};
                 float2* out[1] = {work_buf};
                 add_pass(run_mat.passes[p], 0, 1, in, out, nullptr, 0);
@@ -760,6 +781,7 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
         }
         if (N > 0) {
             for (size_t p = 0; p < B.run_bwd.passes.size(); ++p) {
+                if (p > 0 && B.before_first(B.run_bwd.passes[p])) break;
                 in1[0] = (p == 0 && ext) ? ext_ptr : mainb;
                 out1[0] = mainb;
                 B.add_pass(B.run_bwd.passes[p], 0, 1, in1, out1, nullptr, 0);
@@ -800,6 +822,7 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
         const Run& run = B.run_fwd[0];
         for (size_t p = 0; p < run.passes.size(); ++p) {
             const RunPass& rp = run.passes[p];
+            if (N > 0 && p > 0 && B.after_last(rp)) break;
             in1[0] = (p == 0 && ext) ? ext_ptr : mainb;
             out1[0] = mainb;
             std::vector<float2*> sp;

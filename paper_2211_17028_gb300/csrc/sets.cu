@@ -459,6 +459,12 @@ int engine_prepare_sets(Handle& h, const nqs_state* psi, const nqs_state* v, voi
                           bool save_fwd) {
         for (size_t p = 0; p < run.passes.size(); ++p) {
             const RunPass& rp = run.passes[p];
+            // the backward sweep is done once phi of the first site is saved, the
+            // forward one once chi of the last site is
+            if (p > 0 && !rp.lin.empty()) {
+                if (bwd && *std::max_element(rp.lin.begin(), rp.lin.end()) < plan.site_pos[0]) break;
+                if (save_fwd && *std::min_element(rp.lin.begin(), rp.lin.end()) > plan.site_pos[N - 1]) break;
+            }
             std::vector<DevOp> ops(run_ops.begin() + rp.op_off, run_ops.begin() + rp.op_off + rp.n_ops);
             for (DevOp& d : ops)
                 if (d.type == OP_SITE && save_fwd)
