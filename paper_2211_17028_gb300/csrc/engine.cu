@@ -44,9 +44,10 @@ int cuda_err(cudaError_t e) { return e == cudaSuccess ? NQS_OK : NQS_ERR_CUDA; }
 // The operations (execution order) are grouped into phases: a phase gathers
 // consecutive operations whose dense qubits fit in the RB register qubits;
 // diagonal operations never constrain it.  Each phase pads its register set
-// with the highest free tile positions, gives the lane bits to the lowest
-// free position of each residue class mod 5 (the bank bits of the swizzled
-// transpose buffer) and the warp bits to the rest.  Returns the offsets
+// with the highest free tile positions, gives lane bits 0-3 to the lowest
+// free position of each residue class mod 4 (the bank-pair bits of the
+// swizzled 64-bit re-layout buffer), lane bit 4 to the lowest free position
+// left and the warp bits to the rest.  Returns the offsets
 // (in words) of the operations and matrices and the phase count.
 
 
@@ -94,12 +95,15 @@ ProgInfo build_program(const std::vector<DevOp>& dops, int off, int n, int RB, c
                 used[q] = 1;
             }
         std::sort(R.begin(), R.end());
+        // lanes 0-3 (a half-warp) on free positions of distinct residue mod 4
+        // (conflict-free 64-bit re-layouts, see the kernel's swizzle), lowest
+        // first; lane 4 on the lowest free position left
         std::vector<int> lanes;
-        bool res_used[5] = {false, false, false, false, false};
-        for (int q = 0; q < k && (int)lanes.size() < 5; ++q)
-            if (!used[q] && !res_used[q % 5]) {
+        bool res_used[4] = {false, false, false, false};
+        for (int q = 0; q < k && (int)lanes.size() < 4; ++q)
+            if (!used[q] && !res_used[q % 4]) {
                 lanes.push_back(q);
-                res_used[q % 5] = true;
+                res_used[q % 4] = true;
             }
         for (int q : lanes) used[q] = 1;
         for (int q = 0; q < k && (int)lanes.size() < 5; ++q)
@@ -107,7 +111,7 @@ ProgInfo build_program(const std::vector<DevOp>& dops, int off, int n, int RB, c
                 lanes.push_back(q);
                 used[q] = 1;
             }
-        std::sort(lanes.begin(), lanes.end());
+        std::sort(lanes.begin(), lanes.begin() + std::min<size_t>(4, lanes.size()));
         std::vector<int> warps;
         for (int q = 0; q < k; ++q)
             if (!used[q]) warps.push_back(q);

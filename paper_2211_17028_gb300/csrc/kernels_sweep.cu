@@ -35,7 +35,12 @@ constexpr int kChunk = 32;           // contiguous amplitudes per TMA copy (5 lo
 constexpr int kChunks = kT / kChunk;
 constexpr int kSpinLimit = 1 << 24;  // bounded mbarrier wait (~1-2 s with the back-off)
 
-__device__ __forceinline__ int swz(int j) { return j ^ ((j >> 5) & 31) ^ ((j >> 10) & 3); }
+// Swizzle of the re-layout buffer (8-byte complex64 words): bits 4-7 and 8-11
+// of the tile index are folded into bits 0-3, so the bank pair of word j is
+// the XOR of its three 4-bit groups.  Lanes 0-3 of a warp sit on tile
+// positions of distinct residue mod 4 (chosen by the planner), so each
+// half-warp of a 64-bit access touches 16 distinct bank pairs.  XOR-linear.
+__device__ __forceinline__ int swz(int j) { return j ^ ((j >> 4) & 15) ^ ((j >> 8) & 15); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -380,7 +385,7 @@ __device__ __forceinline__ void sweep_body(const PassArgs& P, const int cta, con
     constexpr int NW = NT / 32;
     extern __shared__ __align__(128) unsigned char dyn[];
     float2* pf = reinterpret_cast<float2*>(dyn);                                  // [S][kT] TMA staging
-    float* tr = reinterpret_cast<float*>(dyn + (size_t)S * kT * sizeof(float2));   // [S][2][kT] swizzled
+    float2* tr = reinterpret_cast<float2*>(dyn + (size_t)S * kT * sizeof(float2));   // [S][kT] swizzled
     uint4* prog = reinterpret_cast<uint4*>(dyn + (size_t)S * kT * 16);              // phases, ops, matrices
     double* acc = reinterpret_cast<double*>(prog + P.prog_words);                   // [ev][S][NW][8]
     __shared__ __align__(8) uint64_t bar;
@@ -506,8 +511,7 @@ __device__ __forceinline__ void sweep_body(const PassArgs& P, const int cta, con
 #pragma unroll
                     for (int r = 0; r < E; ++r) {
                         const int j = sr_of(L, r);
-                        tr[(2 * s) * kT + j] = x[s][r].x;
-                        tr[(2 * s + 1) * kT + j] = x[s][r].y;
+                        tr[s * kT + j] = x[s][r];
                     }
                 __syncthreads();
                 make_layout<RB>(L, phases[p], P.local, tid);
@@ -516,7 +520,7 @@ __device__ __forceinline__ void sweep_body(const PassArgs& P, const int cta, con
 #pragma unroll
                     for (int r = 0; r < E; ++r) {
                         const int j = sr_of(L, r);
-                        x[s][r] = make_float2(tr[(2 * s) * kT + j], tr[(2 * s + 1) * kT + j]);
+                        x[s][r] = tr[s * kT + j];
                     }
                 __syncthreads();
             }
