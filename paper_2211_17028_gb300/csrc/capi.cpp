@@ -527,6 +527,20 @@ const char* nqs_strerror(int code) {
     }
 }
 
+int nqs_selftest_bounded_wait(int* status_out, void* stream) {
+    if (!status_out) return NQS_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int* dev = (int*)dev_alloc(sizeof(int), stream);
+    if (!dev) return NQS_ERR_NOMEM;
+    int rc = cudaMemsetAsync(dev, 0xff, sizeof(int), st) == cudaSuccess ? NQS_OK : NQS_ERR_CUDA;
+    if (rc == NQS_OK) rc = selftest_bounded_wait(dev, stream);
+    if (rc == NQS_OK && cudaMemcpyAsync(status_out, dev, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = NQS_ERR_CUDA;
+    if (rc == NQS_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = NQS_ERR_CUDA;
+    dev_free(dev, sizeof(int), stream);
+    return rc;
+}
+
 const char* nqs_version(void) { return "nqs 0.1 (sm_103a)"; }
 
 }  // extern "C"

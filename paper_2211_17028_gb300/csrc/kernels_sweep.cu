@@ -685,6 +685,20 @@ cudaError_t launch_t(int grid, const PassArgs& P, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Failure-detection self-test: the sweep kernels' bounded mbarrier wait on a
+// barrier that nothing ever arrives at.  The wait must give up (after about a
+// second) and report it through the status word, leaving the context usable.
+__global__ void bounded_wait_probe_kernel(int* status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0);
+    if (threadIdx.x == 0) *status = ok ? NQS_OK : NQS_ERR_DEVICE_TIMEOUT;
+}
+
 }  // namespace
 
 // Register qubits per thread for an S-state launch.  Three states with four
@@ -730,6 +744,15 @@ size_t sweep_smem_bytes(int S, int RB, int prog_words, int n_events) {
     if (S == 1) return smem_for<1, 4>(prog_words, n_events);
     if (S == 2) return RB == 4 ? smem_for<2, 4>(prog_words, n_events) : smem_for<2, 3>(prog_words, n_events);
     return RB == 4 ? smem_for<3, 4>(prog_words, n_events) : smem_for<3, 3>(prog_words, n_events);
+}
+
+cudaError_t launch_bounded_wait_probe(int* status, cudaStream_t st) {
+    bounded_wait_probe_kernel<<<1, 32, 0, st>>>(status);
+    return cudaGetLastError();
+}
+
+int selftest_bounded_wait(int* status, void* stream) {
+    return launch_bounded_wait_probe(status, (cudaStream_t)stream) == cudaSuccess ? NQS_OK : NQS_ERR_CUDA;
 }
 
 cudaError_t launch_sweep(int S, int RB, int grid, const PassArgs& P, cudaStream_t st) {

@@ -150,6 +150,8 @@ int engine_launch_list(const Handle& h, nqs_launch_info* out, size_t cap, size_t
 uint64_t engine_workspace_bytes(const Handle& h);
 uint64_t engine_upload_bytes(const Handle& h);
 uint64_t engine_launches_per_call(const Handle& h);
+// bounded-wait self-test (kernels_sweep.cu): status word into `status` (device)
+int selftest_bounded_wait(int* status, void* stream);
 int engine_reduced_matrix(const void* phi, const void* chi, int n, int qubit, double* R_out,
                           void* scratch, size_t scratch_bytes, void* stream);
 size_t engine_reduced_matrix_scratch_bytes(int n);

@@ -139,6 +139,7 @@ int sweep_reg_bits(int S);
 int sweep_blocks_per_sm(int S, int RB, size_t smem);
 size_t sweep_smem_bytes(int S, int RB, int prog_words, int n_events);
 cudaError_t launch_sweep(int S, int RB, int grid, const PassArgs& P, cudaStream_t st);
+cudaError_t launch_bounded_wait_probe(int* status, cudaStream_t st);
 // the passes of many circuits in one launch: unit u runs on blocks
 // [cta_begin[u], cta_begin[u+1]) (device arrays); all units share S and RB
 cudaError_t launch_sweep_batched(int S, int RB, const PassArgs* units, const int* cta_begin, int n_units,

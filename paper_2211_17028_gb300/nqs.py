@@ -117,6 +117,7 @@ _SIGS = {
     "nqs_truncation_bound": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "nqs_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(nqs_info)]),
     "nqs_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]),
+    "nqs_selftest_bounded_wait": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
     "nqs_schedule_launches": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                              ctypes.POINTER(ctypes.c_size_t)]),
     "nqs_get_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
@@ -532,6 +533,13 @@ def nqs_is_proposal(h, mlp, level, alpha, feats, W1, stream=None):
     _check(_lib().nqs_is_proposal(*args, q.ctypes.data, q.size, ctypes.byref(cnt), _stream_ptr(stream)),
            "nqs_is_proposal")
     return q
+
+
+def nqs_selftest_bounded_wait(stream=None):
+    """Status word written by the bounded-wait probe (NQS_ERR_DEVICE_TIMEOUT expected)."""
+    st = ctypes.c_int(-1)
+    _check(_lib().nqs_selftest_bounded_wait(ctypes.byref(st), _stream_ptr(stream)), "nqs_selftest_bounded_wait")
+    return st.value
 
 
 def nqs_destroy(h):
