@@ -390,7 +390,7 @@ void nqs_destroy(nqs_handle h);
 const char* nqs_strerror(int code);
 /* Failure-detection self-test (no counterpart in the paper): runs the sweep
  * kernels' bounded mbarrier wait on a barrier that nothing arrives at.  The
- * wait gives up after about a second; *status_out receives the status word
+ * wait gives up after about two seconds; *status_out receives the status word
  * the kernel wrote (NQS_ERR_DEVICE_TIMEOUT when the bound works).  Returns
  * NQS_OK when the probe ran; the context stays usable afterwards. */
 int nqs_selftest_bounded_wait(int* status_out, void* stream);

@@ -33,7 +33,7 @@ namespace {
 constexpr int kT = 1 << kMaxTileQ;   // amplitudes per state tile
 constexpr int kChunk = 32;           // contiguous amplitudes per TMA copy (5 low qubits)
 constexpr int kChunks = kT / kChunk;
-constexpr int kSpinLimit = 1 << 24;  // bounded mbarrier wait (~1-2 s with the back-off)
+constexpr int kSpinLimit = 1 << 19;  // bounded mbarrier wait: ~2 s with the back-off (~3.8 us per try)
 
 // Swizzle of the re-layout buffer (8-byte complex64 words): bits 4-7 and 8-11
 // of the tile index are folded into bits 0-3, so the bank pair of word j is
@@ -686,8 +686,8 @@ cudaError_t launch_t(int grid, const PassArgs& P, cudaStream_t st) {
 }
 
 // Failure-detection self-test: the sweep kernels' bounded mbarrier wait on a
-// barrier that nothing ever arrives at.  The wait must give up (after about a
-// second) and report it through the status word, leaving the context usable.
+// barrier that nothing ever arrives at.  The wait must give up (after about
+// two seconds) and report it through the status word, leaving the context usable.
 __global__ void bounded_wait_probe_kernel(int* status) {
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) {
