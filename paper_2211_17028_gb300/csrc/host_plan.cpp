@@ -161,6 +161,53 @@ void build_plan(const Circuit& c, const std::vector<Factors>& f, int tile_qubits
         append(gate_op(c.gates[g]));
         flush_sites((int)g);
     }
+    // A dense two-qubit operation that is diagonal up to a Hadamard on one of
+    // its qubits (a CNOT left alone, e.g. when a noise site sits inside a
+    // CNOT-RZ-CNOT) is rewritten as H, diagonal, H on that qubit and the
+    // order is fused again: the diagonal part needs no register qubits and
+    // the Hadamards join neighbouring one-qubit operations where they can.
+    {
+        const double r2 = std::sqrt(0.5);
+        std::array<cd, 16> h{};
+        h[0] = h[1] = h[2] = cd(r2);
+        h[3] = cd(-r2);
+        std::vector<HostOp> old_ops;
+        old_ops.swap(p.ops);
+        bool changed = false;
+        std::vector<HostOp> expanded;
+        for (const HostOp& o : old_ops) {
+            if (o.type == OP_G2) {
+                bool done = false;
+                for (int pos = 1; pos >= 0 && !done; --pos) {
+                    const std::array<cd, 16> h4 = expand_1q(h, pos);
+                    const std::array<cd, 16> m = matmul(h4, matmul(o.m, h4, 4), 4);
+                    if (!is_diag4(m)) continue;
+                    HostOp hg;
+                    hg.type = OP_G1;
+                    hg.q0 = pos == 0 ? o.q0 : o.q1;
+                    hg.m = h;
+                    HostOp d = o;
+                    d.type = OP_D2;
+                    d.m = m;
+                    expanded.push_back(hg);
+                    expanded.push_back(d);
+                    expanded.push_back(hg);
+                    done = changed = true;
+                }
+                if (done) continue;
+            }
+            expanded.push_back(o);
+        }
+        if (!changed) {
+            p.ops.swap(old_ops);
+        } else {
+            std::fill(last.begin(), last.end(), -1);
+            for (const HostOp& o : expanded) {
+                append(o);
+                if (o.type == OP_SITE) p.site_pos[o.site] = (int)p.ops.size() - 1;
+            }
+        }
+    }
     // exact zeros for the off-diagonals of diagonal operations
     for (auto& o : p.ops) {
         if (o.type == OP_D1) o.m[1] = o.m[2] = cd(0);

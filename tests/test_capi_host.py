@@ -151,7 +151,8 @@ def test_plan_shapes():
     info = nqs.nqs_get_info(h)
     assert info["n_qubits"] == 30 and info["n_sites"] == 20 and info["tile_qubits"] == 12
     # CNOT-RZ-CNOT collapses into one diagonal phase: far fewer fused ops than gates
-    assert info["n_ops"] <= 30 + 4 * (45 + 30) + 20
+    # (a noise inside a block leaves its two CNOTs, each at most H, diagonal, H)
+    assert info["n_ops"] <= 30 + 4 * (45 + 30) + 20 + 4 * 20
     assert info["n_passes"] >= 3
     nqs.nqs_destroy(h)
     h = _handle(W.c1_line6())
