@@ -10,7 +10,7 @@ from oracle import csim
 from oracle import expansion as OEX
 from oracle import ir as OIR
 
-# spec tolerance: every fidelity within 1e-5 relative of the FP64 oracle;
+# tolerance: every fidelity within 1e-5 relative of the FP64 oracle;
 # T_u, per-site-set sums and individual terms within 1e-5 * F absolute
 REL_TOL = 1e-5
 
