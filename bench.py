@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--workload", default="qaoa30_l2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--launch-list", default=None,
+                    help="write the timed schedule's launch list (nqs_schedule_launches) to this JSON file")
     return ap.parse_args()
 
 
@@ -310,6 +312,9 @@ def run_nqs(args):
     except Exception:
         pass
 
+    if args.launch_list and rank == 0:
+        with open(args.launch_list, "w") as f:
+            json.dump(nqs.nqs_schedule_launches(h), f)
     # end to end through the public API from host data (the timed handle's
     # workspace is released first: the checkpoints of one call fill most of HBM)
     circ.close()
