@@ -1,7 +1,7 @@
-"""O2 / O4: the level-l approximation of Algorithm 1, literally, in FP64
-(oracle; test infrastructure only).
+"""O2 / O4: the level-l approximation of Sec. IV in FP64 (oracle; test
+infrastructure only).
 
-Steps, in the paper's order and notation (Sec. III-IV):
+The oracle first lists the kept assignments, then evaluates each one:
 
 1. matrix representation of each noise, M_E = sum_k E_k (x) E_k^*  (Sec. III);
 2. tensor permutation M -> M~: with M's edges (1,2) as row and (3,4) as
@@ -9,16 +9,17 @@ Steps, in the paper's order and notation (Sec. III-IV):
 3. SVD M~ = S D T^dagger with d_0 the largest singular value;
    U~_i = d_i S|i>, V~_i = T|i>, so M~ = sum_i U~_i V~_i^dagger (Fig. 3b);
 4. tensor permutation back: M = sum_i U_i (x) V_i (Fig. 3c);
-5. Algorithm 1: for every level k <= l, every site set p_1 < ... < p_k and
-   every choice of a non-dominant factor i in {1,2,3} at those sites (the
-   dominant factor U_0 (x) V_0 everywhere else), the double-size network
-   splits into the network on the original wires (gates U, factors U_i) and
-   the one on the conjugate wires (gates U^*, factors V_i); both are
-   contracted -- here by a plain state-vector sweep -- and multiplied;
-   T_k sums those products and A(l) = sum_{k<=l} T_k.
+5. kept assignments (O4): every level k <= l, every site set p_1 < ... < p_k
+   and every choice of a non-dominant factor i in {1,2,3} at those sites,
+   the dominant factor U_0 (x) V_0 everywhere else (Algorithm 1);
+6. each kept assignment splits the double-size network into the network on
+   the original wires (gates U, factors U_i) and the one on the conjugate
+   wires (gates U^*, factors V_i); both are contracted -- here by a plain
+   state-vector sweep -- and multiplied; T_k sums those products and
+   A(l) = sum_{k<=l} T_k.
 
-O4 is the canonical list of kept assignments in exactly that loop order
-(level, then site tuple lexicographic, then factor tuple lexicographic),
+O4's order is the record format shared with the library's enumerator:
+level, then site tuple lexicographic, then factor tuple lexicographic,
 packed as 64-bit records: bits 0-3 the level u, then for r = 0..u-1 a 14-bit
 field at bit 4 + 14 r holding the site index (12 bits) and, above it, the
 factor index (2 bits).

@@ -449,6 +449,74 @@ def test_truncation_error_within_bounds(seed):
     assert math.isclose(B.theorem1_bound(N, p, 1), tail, rel_tol=1e-12)
 
 
+def _per_site_by_subsets(norms, level):
+    """Brute force over every site set S with |S| > level of
+    prod_{s in S} a_s prod_{s not in S} b_s, with (a_s, b_s) given."""
+    N = len(norms)
+    tot = []
+    for k in range(level + 1, N + 1):
+        for S in itertools.combinations(range(N), k):
+            term = 1.0
+            for s in range(N):
+                term *= norms[s][0] if s in S else norms[s][1]
+            tot.append(term)
+    return math.fsum(tot)
+
+
+def test_per_site_bound_identical_depolarizing_is_a_binomial_tail():
+    # paper-form depolarizing: M' = (1-p) I(x)I and M-bar = p/3 (X(x)X - Y(x)Y + Z(x)Z),
+    # whose eigenvalues on the Bell basis are p/3 * {3, -1, -1, -1}: ||M-bar|| = p,
+    # ||M'|| = 1 - p, so for N identical sites the bound is P[Binomial(N, p) > l]
+    from scipy.stats import binom
+    for N, p in ((1, 0.2), (5, 0.03), (12, 0.01), (20, 0.004)):
+        kl = [ch.depolarizing_paper(p)] * N
+        for lvl in range(0, min(N, 4) + 1):
+            want = float(binom.sf(lvl, N, p))
+            got = B.per_site_bound(kl, lvl)
+            assert math.isclose(got, want, rel_tol=1e-9, abs_tol=1e-300), (N, p, lvl, got, want)
+    # the swapped norms would give P[Binomial(N, 1-p) > l], close to 1
+    assert B.per_site_bound([ch.depolarizing_paper(0.01)] * 10, 1) < 5e-3
+
+
+def test_per_site_bound_mixed_channels_brute_force():
+    # phase damping: M~ restricted to {|00>, |11>} is [[1, r], [r, 1]] with
+    # r = sqrt(1 - lambda); M' = (1 + r)/2 I(x)I, M-bar = (1 - r)/2 Z(x)Z^*
+    def pd_norms(lam):
+        r = math.sqrt(1.0 - lam)
+        return ((1.0 - r) / 2.0, (1.0 + r) / 2.0)
+    chans = [("dep", 0.02), ("pd", 0.05), ("dep", 0.001), ("pd", 0.3), ("dep", 0.1), ("pd", 0.01)]
+    kl, norms = [], []
+    for kind, r in chans:
+        if kind == "dep":
+            kl.append(ch.depolarizing_paper(r))
+            norms.append((r, 1.0 - r))
+        else:
+            kl.append(ch.phase_damping(r))
+            norms.append(pd_norms(r))
+    for lvl in range(len(chans)):
+        want = _per_site_by_subsets(norms, lvl)
+        assert math.isclose(B.per_site_bound(kl, lvl), want, rel_tol=1e-12), lvl
+    assert B.per_site_bound(kl, len(chans)) == 0.0
+
+
+def test_theorem1_bound_hand_values():
+    # (1+8p)^N expands binomially as sum_i C(N,i) (4p)^i (1+4p)^(N-i); the bound is its tail.
+    # p = 1/100: N=2, l=0: 1.08^2 - 1.04^2 = 0.0848; l=1: (0.04)^2 = 0.0016;
+    # N=3, l=1: 3 (0.04)^2 1.04 + 0.04^3 = 0.005056; N=3, l=2: 0.04^3 = 6.4e-5
+    assert math.isclose(B.theorem1_bound(2, 0.01, 0), 0.0848, rel_tol=1e-12)
+    assert math.isclose(B.theorem1_bound(2, 0.01, 1), 0.0016, rel_tol=1e-12)
+    assert math.isclose(B.theorem1_bound(3, 0.01, 1), 0.005056, rel_tol=1e-12)
+    assert math.isclose(B.theorem1_bound(3, 0.01, 2), 6.4e-5, rel_tol=1e-9)
+    assert B.theorem1_bound(3, 0.01, 5) == 0.0
+    # level-1 corollary, hand value: 32 sqrt(e) 10^2 (1e-3)^2 = 0.005275908...
+    assert math.isclose(B.level1_corollary(10, 1e-3), 0.0052759080662, rel_tol=1e-10)
+    # and it dominates the level-1 tail whenever p <= 1/(8N), as the paper's corollary states
+    for N in (1, 2, 5, 20, 100):
+        for f in (1.0, 0.5, 0.1, 0.01):
+            p = f / (8 * N)
+            assert B.theorem1_bound(N, p, 1) <= B.level1_corollary(N, p)
+
+
 def test_level1_error_grows_quadratically_in_rate():
     # Fig. 6 trend: level-1 error ~ p^2
     errs = []
@@ -518,3 +586,20 @@ def test_planted_mistakes_are_caught(monkeypatch):
     assert not _pins_pass()
     monkeypatch.setattr(EX, "_network_amplitude", good_net)
     assert _pins_pass()
+
+    # 6. per-site bound with ||M'|| and ||M-bar|| swapped, and 7. Theorem 1 with
+    # the head summed one level short: the bound pins must fail
+    good_dar = B.dominant_and_rest
+    monkeypatch.setattr(B, "dominant_and_rest", lambda k: tuple(reversed(good_dar(k))))
+    with pytest.raises(AssertionError):
+        test_per_site_bound_identical_depolarizing_is_a_binomial_tail()
+    with pytest.raises(AssertionError):
+        test_per_site_bound_mixed_channels_brute_force()
+    monkeypatch.setattr(B, "dominant_and_rest", good_dar)
+    good_t1 = B.theorem1_bound
+    monkeypatch.setattr(B, "theorem1_bound", lambda N, p, l: good_t1(N, p, max(l - 1, 0)))
+    with pytest.raises(AssertionError):
+        test_theorem1_bound_hand_values()
+    monkeypatch.setattr(B, "theorem1_bound", good_t1)
+    test_per_site_bound_identical_depolarizing_is_a_binomial_tail()
+    test_theorem1_bound_hand_values()
