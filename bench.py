@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--workload", default="qaoa30_l2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--jit", default="auto", choices=["auto", "on", "off"],
+                    help="pass-specialised sweep kernels (NQS_OPT_JIT): automatic, always, never")
     ap.add_argument("--launch-list", default=None,
                     help="write the timed schedule's launch list (nqs_schedule_launches) to this JSON file")
     return ap.parse_args()
@@ -257,6 +259,8 @@ def run_nqs(args):
     text = W.to_ir_text(w)
     circ = nqs.NoisyCircuit(text)
     h = circ.h
+    jit_opt = {"auto": 0, "on": 1, "off": 2}[args.jit]
+    nqs.nqs_set_option(h, nqs.NQS_OPT_JIT, jit_opt)
     psi, v = nqs.basis(0), (nqs.ideal() if w.v["kind"] == "ideal" else nqs.basis(w.v["bits"]))
     stream = torch.cuda.current_stream()
 
@@ -265,8 +269,12 @@ def run_nqs(args):
     pinned = torch.empty((args.steps + args.warmup + 1) * rsz, dtype=torch.uint8, pin_memory=True)
     slot = lambda i: nqs.nqs_result.from_address(pinned.data_ptr() + i * rsz)
 
+    t_build = time.perf_counter()
     for i in range(args.warmup):
         nqs.nqs_fidelity(h, psi, v, level, stream, out=slot(i))
+        if i == 0:
+            torch.cuda.synchronize()
+            t_build = time.perf_counter() - t_build
     torch.cuda.synchronize()
     info = nqs.nqs_get_info(h)
     n_terms = int(slot(0).n_terms)
@@ -327,6 +335,7 @@ def run_nqs(args):
         for _ in range(k2):
             hh = nqs.nqs_load_circuit(text)
             nqs.nqs_prepare_noise(hh)
+            nqs.nqs_set_option(hh, nqs.NQS_OPT_JIT, jit_opt)
             r = nqs.nqs_fidelity(hh, psi, v, level, stream)   # pageable result: synchronous read-back
             up += nqs.nqs_get_info(hh)["upload_bytes"]
             nqs.nqs_destroy(hh)
@@ -368,7 +377,9 @@ def run_nqs(args):
             "cpu_baseline": cpu,
             "result": {"F": res["F"], "T": res["T"], "bound": res["bound"], "status": res["status"]},
             "plan": {"ops": info["n_ops"], "passes": info["n_passes"], "tile_qubits": info["tile_qubits"],
-                     "workspace_gib": info["workspace_bytes"] / 2 ** 30},
+                     "workspace_gib": info["workspace_bytes"] / 2 ** 30,
+                     "jit_launches": info["jit_launches"], "jit_state": info["jit_state"],
+                     "first_call_s": t_build},
         }
         print(json.dumps(line))
     if world > 1:

@@ -181,6 +181,8 @@ typedef struct {
     uint64_t launches_per_call; /* kernels launched by one nqs_fidelity call */
     int32_t ckpt_spacing;       /* sites per checkpoint block of the current schedule (0: every site) */
     int32_t n_states;           /* 2^n-amplitude state buffers held by the current schedule */
+    int32_t jit_launches;       /* sweep launches of the current schedule that run pass-specialised kernels */
+    int32_t jit_state;          /* 0 not requested, 1 built, -1 requested but NVRTC or a compile failed */
 } nqs_info;
 
 int nqs_get_info(nqs_handle h, nqs_info* out);
@@ -192,7 +194,8 @@ int nqs_get_info(nqs_handle h, nqs_info* out);
  * together, register qubits per thread (0: shared-memory tile kernel), phases
  * of the register-resident program, grid size, operation counts
  * ops[] = {dense 1-qubit, dense 2-qubit, diagonal 1-qubit, diagonal 2-qubit,
- * noise sites, site reductions, spawned states, checkpoint saves} and the
+ * noise sites, site reductions, spawned states, checkpoint saves}, whether
+ * the pass runs a pass-specialised kernel (NQS_OPT_JIT) and the
  * algorithmic bytes of the launch (see nqs_kernel_stats).  Call with out =
  * NULL (or cap too small) to get the count only.  No counterpart in the paper. */
 typedef struct {
@@ -202,7 +205,7 @@ typedef struct {
     int32_t phases;
     int32_t grid;
     int32_t ops[8];
-    int32_t pad_;
+    int32_t jit;                /* 1: the pass runs a pass-specialised kernel */
     double algorithmic_bytes;
 } nqs_launch_info;
 
@@ -223,12 +226,19 @@ int nqs_schedule_launches(nqs_handle h, nqs_launch_info* out, size_t cap, size_t
  *       passes: 3 (512-thread blocks) or 4 (256-thread blocks).
  *   NQS_OPT_MAX_OPS       fused operations per pass, 8..160 (default 96).
  *   NQS_OPT_MAX_SITES     noise sites per pass, 1..8 (default 4).
+ *   NQS_OPT_JIT           sweep passes of 12-qubit tiles run kernels generated
+ *       for each pass (operations, layouts and matrices compiled in as
+ *       constants; NVRTC at schedule build time, cached for the process):
+ *       0 automatic (circuits of 26 qubits or more), 1 always, 2 never (the
+ *       interpreting kernel).  When NVRTC cannot be loaded the interpreting
+ *       kernel runs; nqs_info.jit_launches tells which ran.
  * NQS_ERR_ARG for an unknown option or a value out of range; NQS_ERR_ORDER
  * for the two segmentation options before nqs_prepare_noise. */
 #define NQS_OPT_CKPT_SPACING 1
 #define NQS_OPT_SWEEP_RB 2
 #define NQS_OPT_MAX_OPS 3
 #define NQS_OPT_MAX_SITES 4
+#define NQS_OPT_JIT 5
 
 int nqs_set_option(nqs_handle h, int option, int64_t value);
 int nqs_get_option(nqs_handle h, int option, int64_t* value);

@@ -23,10 +23,25 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
 
 
+def _includes(path, seen):
+    """The quoted #include files that `path` pulls in, recursively."""
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return seen
+    for ln in lines:
+        ln = ln.strip()
+        if ln.startswith("#include \""):
+            dep = os.path.normpath(os.path.join(os.path.dirname(path), ln.split('"')[1]))
+            if dep not in seen and os.path.exists(dep):
+                seen.add(dep)
+                _includes(dep, seen)
+    return seen
+
+
 def _compile(src, extra):
     obj = os.path.join(OUT, os.path.basename(src) + ".o")
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
-    headers.append(os.path.join(HERE, "..", "include", "nqs.h"))
+    headers = sorted(_includes(src, set()))
     newest = max(os.path.getmtime(p) for p in headers + [src])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest and not extra.get("force"):
         return obj
@@ -34,8 +49,6 @@ def _compile(src, extra):
            "-Xcompiler", "-O2", "--expt-relaxed-constexpr"] + ARCH
     if extra.get("verbose_ptxas") and src.endswith(".cu"):
         cmd.append("-Xptxas=-v")
-    if src.endswith(".cpp"):
-        cmd = cmd[:3] + ["-x", "cu"] + cmd[3:] if False else cmd
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))
@@ -53,7 +66,7 @@ def build(force=False, verbose_ptxas=False):
     newest = max(os.path.getmtime(o) for o in objs)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
         tmp = LIB + ".tmp%d" % os.getpid()
-        cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static"]
+        cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static", "-ldl", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

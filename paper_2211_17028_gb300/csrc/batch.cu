@@ -309,7 +309,7 @@ int engine_batch_fidelity(Handle** hs, size_t count, const nqs_state* psis, cons
             if (!h.eng) h.eng = new Engine();
             rc = engine_init(*h.eng);
             if (rc == NQS_OK) rc = build_schedule(h, *h.eng, &psis[k], &vs[k], std::min(levels[k], (int)h.factors.size()),
-                                                  stream);
+                                                  stream, false);
             P->engines[k] = h.eng;
             P->gens[k] = h.eng->gen;
         }

@@ -264,6 +264,9 @@ int nqs_get_info(nqs_handle hh, nqs_info* out) {
     int n_states = 0;
     out->ckpt_spacing = engine_spacing(*h, &n_states);
     out->n_states = n_states;
+    int js = 0;
+    out->jit_launches = engine_jit_info(*h, &js);
+    out->jit_state = js;
     return NQS_OK;
 }
 
@@ -296,6 +299,10 @@ int nqs_set_option(nqs_handle hh, int option, int64_t value) {
             if (value != 0 && value != 3 && value != 4) return NQS_ERR_ARG;
             h->opt_rb_multi = (int)value;
             break;
+        case NQS_OPT_JIT:
+            if (value > 2) return NQS_ERR_ARG;
+            h->opt_jit = (int)value;
+            break;
         case NQS_OPT_MAX_OPS:
         case NQS_OPT_MAX_SITES: {
             if (!h->prepared) return NQS_ERR_ORDER;
@@ -318,6 +325,7 @@ int nqs_get_option(nqs_handle hh, int option, int64_t* value) {
     switch (option) {
         case NQS_OPT_CKPT_SPACING: *value = h->opt_spacing; break;
         case NQS_OPT_SWEEP_RB: *value = h->opt_rb_multi; break;
+        case NQS_OPT_JIT: *value = h->opt_jit; break;
         case NQS_OPT_MAX_OPS: *value = h->opt_max_ops; break;
         case NQS_OPT_MAX_SITES: *value = h->opt_max_sites; break;
         default: return NQS_ERR_ARG;

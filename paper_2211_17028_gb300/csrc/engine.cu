@@ -26,6 +26,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <vector>
@@ -36,6 +38,12 @@ namespace nqs {
 
 
 int cuda_err(cudaError_t e) { return e == cudaSuccess ? NQS_OK : NQS_ERR_CUDA; }
+
+// NQS_JIT=0 in the environment turns the automatic choice of pass-specialised kernels off
+static bool jit_env_enabled() {
+    const char* e = std::getenv("NQS_JIT");
+    return !(e && e[0] == '0');
+}
 
 
 
@@ -597,6 +605,9 @@ void engine_release(Engine& E, void* stream) {
     E.buf_bytes = E.aux_bytes = 0;
     E.level = -1;
     E.launches.clear();
+    E.jit.clear();
+    E.jit_launches = 0;
+    E.jit_state = 0;
 }
 
 // States held by a schedule that keeps phi every `k` sites: the block
@@ -621,12 +632,16 @@ static int best_spacing(int N, int level) {
 }
 
 // Build (or reuse) the schedule for this level and state kinds.
-int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* v, int level,
-                          void* stream) {
+int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* v, int level, void* stream,
+                   bool allow_jit) {
     const Plan& plan = h.plan;
     const int N = (int)h.factors.size();
+    // automatic: circuits of 26 qubits or more, where one call's sweeps outlast
+    // the compilation of its distinct passes
+    const bool want_jit =
+        allow_jit && (h.opt_jit == 1 || (h.opt_jit == 0 && plan.n >= 26 && jit_env_enabled()));
     if (E.level == level && E.psi_kind == psi->kind && E.v_kind == v->kind && E.psi_bits == psi->bits &&
-        E.v_bits == v->bits && E.psi_dev == psi->dev && E.v_dev == v->dev)
+        E.v_bits == v->bits && E.psi_dev == psi->dev && E.v_dev == v->dev && !(want_jit && E.jit_state == 0))
         return NQS_OK;
     engine_release(E, stream);
     ++E.gen;
@@ -871,6 +886,41 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
         engine_release(E, stream);
         return NQS_ERR_UNSUPPORTED;
     }
+    // pass-specialised kernels for the register-resident passes
+    if (want_jit && B.rt) {
+        std::vector<JitPass*> todo;
+        std::vector<Launch*> owner;
+        for (auto& l : B.L) {
+            if (l.kind != L_PASS || !l.rt) continue;
+            std::unique_ptr<JitPass> jp(new JitPass());
+            jp->S = l.S;
+            jp->RB = l.rb;
+            jp->n = plan.n;
+            for (int j = 0; j < kMaxTileQ; ++j) jp->local[j] = l.args.local[j];
+            for (int j = 0; j < kMaxQ; ++j) jp->nonlocal[j] = l.args.nonlocal[j];
+            jp->n_events = l.args.n_events;
+            const uint4* w = B.prog.data() + l.prog_index;
+            const DevPhase* phs = reinterpret_cast<const DevPhase*>(w);
+            jp->phases.assign(phs, phs + l.args.n_phases);
+            const OpRec* ops = reinterpret_cast<const OpRec*>(w + l.args.ops_word);
+            jp->ops.assign(ops, ops + (l.args.mats_word - l.args.ops_word));
+            const float2* mts = reinterpret_cast<const float2*>(w + l.args.mats_word);
+            jp->mats.assign(mts, mts + 2 * (l.args.prog_words - l.args.mats_word));
+            todo.push_back(jp.get());
+            owner.push_back(&l);
+            E.jit.push_back(std::move(jp));
+        }
+        std::string err;
+        if (!todo.empty() && jit_build(todo, &err) == 0) {
+            for (size_t i = 0; i < todo.size(); ++i) owner[i]->jit = todo[i];
+            E.jit_launches = (int)todo.size();
+            E.jit_state = 1;
+        } else {
+            E.jit.clear();
+            E.jit_state = todo.empty() ? 0 : -1;
+            if (!todo.empty() && std::getenv("NQS_JIT_VERBOSE")) std::fprintf(stderr, "nqs jit: %s\n", err.c_str());
+        }
+    }
 
     // --- aux allocation: ops, mats, ckpt table, kmats, descs, partials, term values, level offsets, result
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -966,6 +1016,7 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
 }
 
 int launch_pass(const Launch& l, cudaStream_t st) {
+    if (l.jit) return cuda_err(jit_launch(*l.jit, l.grid, l.args, st));
     if (l.rt) return cuda_err(launch_sweep(l.S, l.rb, l.grid, l.args, st));
     return cuda_err(launch_tile_pass(l.S, l.grid, l.smem, l.args, st));
 }
@@ -1109,10 +1160,16 @@ int engine_launch_list(const Handle& h, nqs_launch_info* out, size_t cap, size_t
             o.phases = l.rt ? l.args.n_phases : 0;
             o.grid = l.grid;
             for (int c = 0; c < 8; ++c) o.ops[c] = l.op_counts[c];
+            o.jit = l.jit ? 1 : 0;
             o.algorithmic_bytes = l.bytes;
         }
     }
     return NQS_OK;
+}
+
+int engine_jit_info(const Handle& h, int* state) {
+    *state = (h.eng && h.eng->level >= 0) ? h.eng->jit_state : 0;
+    return (h.eng && h.eng->level >= 0) ? h.eng->jit_launches : 0;
 }
 
 int engine_spacing(const Handle& h, int* n_states) {

@@ -4,8 +4,10 @@
 
 #include <cuda_runtime.h>
 
+#include <memory>
 #include <vector>
 
+#include "jit.h"
 #include "nqs_internal.h"
 #include "sweep_types.h"
 
@@ -49,6 +51,7 @@ struct Launch {
     double bytes = 0;                // algorithmic bytes (pass kernels)
     bool bd_table = false;           // pass saves through the block-boundary checkpoint table
     int op_counts[8] = {};           // pass: G1, G2, D1, D2, sites, reductions, spawned states, saves
+    JitPass* jit = nullptr;          // pass-specialised kernel (owned by the engine), or the interpreter
 };
 
 struct Engine {
@@ -90,6 +93,9 @@ struct Engine {
     uint64_t gen = 0;                // bumped whenever the schedule is rebuilt
     int spacing = 0;                 // sites per checkpoint block of the current schedule (0: every site)
     size_t n_states = 0;             // state buffers of the current schedule
+    std::vector<std::unique_ptr<JitPass>> jit;   // pass-specialised kernels of the current schedule
+    int jit_launches = 0;
+    int jit_state = 0;               // 0 not requested, 1 built, -1 failed (interpreter runs)
 };
 
 
@@ -127,7 +133,10 @@ Run make_run(const Plan& plan, const std::vector<PassSpec>& segs, RunType rt, bo
 // schedule construction and execution (engine.cu)
 int engine_init(Engine& E);
 void engine_release(Engine& E, void* stream);
-int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* v, int level, void* stream);
+// allow_jit: the schedule may use pass-specialised kernels (the batch executor
+// launches passes through its own multi-circuit kernel and passes false)
+int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* v, int level, void* stream,
+                   bool allow_jit = true);
 int run_schedule(Handle& h, Engine& E, cudaStream_t st);
 int run_launch(Handle& h, Engine& E, const Launch& l, cudaStream_t st);
 int launch_pass(const Launch& l, cudaStream_t st);

@@ -122,6 +122,7 @@ struct Handle {
     int opt_rb_multi = 0;          // register qubits of multi-state sweeps (3 or 4)
     int opt_max_ops = 0;           // operations per pass (segmentation)
     int opt_max_sites = 0;         // sites per pass (segmentation)
+    int opt_jit = 0;               // pass-specialised kernels: 0 auto, 1 always, 2 never
 };
 
 // engine entry points (engine.cu)
@@ -150,6 +151,7 @@ int engine_launch_list(const Handle& h, nqs_launch_info* out, size_t cap, size_t
 uint64_t engine_workspace_bytes(const Handle& h);
 uint64_t engine_upload_bytes(const Handle& h);
 uint64_t engine_launches_per_call(const Handle& h);
+int engine_jit_info(const Handle& h, int* state);
 // bounded-wait self-test (kernels_sweep.cu): status word into `status` (device)
 int selftest_bounded_wait(int* status, void* stream);
 int engine_reduced_matrix(const void* phi, const void* chi, int n, int qubit, double* R_out,

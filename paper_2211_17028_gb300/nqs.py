@@ -35,6 +35,7 @@ NQS_OPT_CKPT_SPACING = 1
 NQS_OPT_SWEEP_RB = 2
 NQS_OPT_MAX_OPS = 3
 NQS_OPT_MAX_SITES = 4
+NQS_OPT_JIT = 5
 
 
 class NqsError(RuntimeError):
@@ -77,13 +78,13 @@ class nqs_info(ctypes.Structure):
                 ("n_ops", ctypes.c_int32), ("n_passes", ctypes.c_int32), ("tile_qubits", ctypes.c_int32),
                 ("workspace_bytes", ctypes.c_uint64), ("upload_bytes", ctypes.c_uint64),
                 ("launches_per_call", ctypes.c_uint64), ("ckpt_spacing", ctypes.c_int32),
-                ("n_states", ctypes.c_int32)]
+                ("n_states", ctypes.c_int32), ("jit_launches", ctypes.c_int32), ("jit_state", ctypes.c_int32)]
 
 
 class nqs_launch_info(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("states", ctypes.c_int32), ("reg_qubits", ctypes.c_int32),
                 ("phases", ctypes.c_int32), ("grid", ctypes.c_int32), ("ops", ctypes.c_int32 * 8),
-                ("pad_", ctypes.c_int32), ("algorithmic_bytes", ctypes.c_double)]
+                ("jit", ctypes.c_int32), ("algorithmic_bytes", ctypes.c_double)]
 
 
 class nqs_kernel_stats(ctypes.Structure):
@@ -363,7 +364,7 @@ def nqs_schedule_launches(h):
     for i in range(cnt.value):
         r = buf[i]
         d = {"kind": LAUNCH_KINDS[r.kind], "states": r.states, "reg_qubits": r.reg_qubits, "phases": r.phases,
-             "grid": r.grid, "algorithmic_bytes": r.algorithmic_bytes}
+             "grid": r.grid, "jit": r.jit, "algorithmic_bytes": r.algorithmic_bytes}
         d.update({k: r.ops[j] for j, k in enumerate(OP_COUNT_NAMES)})
         out.append(d)
     return out

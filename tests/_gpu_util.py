@@ -9,6 +9,7 @@ import workloads as W
 from oracle import csim
 from oracle import expansion as OEX
 from oracle import ir as OIR
+from oracle import o3 as O3
 
 # tolerance: every fidelity within 1e-5 relative of the FP64 oracle;
 # T_u, per-site-set sums and individual terms within 1e-5 * F absolute
@@ -16,9 +17,18 @@ REL_TOL = 1e-5
 
 
 def oracle_result(w, level, keep_terms=True):
+    """O2 (one sweep per network per term) up to 10 qubits, O3 (checkpointed,
+    pinned to O2) above; the same dict either way."""
     c = OIR.parse(W.to_ir_text(w))
-    fn = csim.term_value if w.n > 10 else None
-    return OEX.approximate(c, w.psi, w.v, level, keep_terms=keep_terms, amplitude_fn=fn)
+    if w.n <= 10:
+        return OEX.approximate(c, w.psi, w.v, level, keep_terms=keep_terms)
+    r = O3.approximate(c, w.psi, w.v, level)
+    if keep_terms:
+        recs = OEX.enumerate_records(len(c.noises), min(level, len(c.noises)))
+        r["terms"] = list(zip(recs, r["terms"]))
+    else:
+        r["terms"] = []
+    return r
 
 
 def gpu_state(spec, n):
