@@ -63,6 +63,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--jit", default="auto", choices=["auto", "on", "off"],
                     help="pass-specialised sweep kernels (NQS_OPT_JIT): automatic, always, never")
+    ap.add_argument("--rb", type=int, default=0, choices=[0, 3, 4],
+                    help="register qubits of multi-state sweep passes (NQS_OPT_SWEEP_RB; 0 automatic)")
     ap.add_argument("--launch-list", default=None,
                     help="write the timed schedule's launch list (nqs_schedule_launches) to this JSON file")
     return ap.parse_args()
@@ -261,6 +263,8 @@ def run_nqs(args):
     h = circ.h
     jit_opt = {"auto": 0, "on": 1, "off": 2}[args.jit]
     nqs.nqs_set_option(h, nqs.NQS_OPT_JIT, jit_opt)
+    if args.rb:
+        nqs.nqs_set_option(h, nqs.NQS_OPT_SWEEP_RB, args.rb)
     psi, v = nqs.basis(0), (nqs.ideal() if w.v["kind"] == "ideal" else nqs.basis(w.v["bits"]))
     stream = torch.cuda.current_stream()
 
@@ -314,7 +318,7 @@ def run_nqs(args):
     try:
         with open(os.path.join(ROOT, "profiles", "sweep_traffic.json")) as f:
             tr = json.load(f)
-        if (tr.get("workload") == args.workload and tr.get("kernel_source_sha") == kernel_source_sha()
+        if (tr.get("workload") == args.workload and tr.get("kernel_source_sha") == kernel_source_sha(info["jit_launches"] > 0)
                 and tr.get("kernel") == ("multi" if dom is multi else "single")):
             traffic = tr.get("dram_bytes_per_launch")
     except Exception:
@@ -336,6 +340,8 @@ def run_nqs(args):
             hh = nqs.nqs_load_circuit(text)
             nqs.nqs_prepare_noise(hh)
             nqs.nqs_set_option(hh, nqs.NQS_OPT_JIT, jit_opt)
+            if args.rb:
+                nqs.nqs_set_option(hh, nqs.NQS_OPT_SWEEP_RB, args.rb)
             r = nqs.nqs_fidelity(hh, psi, v, level, stream)   # pageable result: synchronous read-back
             up += nqs.nqs_get_info(hh)["upload_bytes"]
             nqs.nqs_destroy(hh)
@@ -387,9 +393,11 @@ def run_nqs(args):
     return 0
 
 
-def kernel_source_sha():
+def kernel_source_sha(jit=False):
+    """Hash of the source that defines the timed sweep kernel: the pass
+    generator when pass-specialised kernels ran, else the interpreting kernel."""
     import hashlib
-    p = os.path.join(ROOT, "paper_2211_17028_gb300", "csrc", "kernels_sweep.cu")
+    p = os.path.join(ROOT, "paper_2211_17028_gb300", "csrc", "jit.cpp" if jit else "kernels_sweep.cu")
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 

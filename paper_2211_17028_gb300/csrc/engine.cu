@@ -277,6 +277,7 @@ struct Builder {
     std::vector<uint4> prog;          // programs of the register-resident launches
     bool too_big = false;             // a launch would not fit in shared memory
     bool rt = false;                  // register-resident kernel (tile of exactly 12 qubits)
+    bool use_jit = false;             // passes will get pass-specialised kernels
     std::vector<FinishDesc> descs;
     std::vector<Launch> L;
     size_t partial_doubles = 0;
@@ -353,7 +354,9 @@ struct Builder {
         l.op_index = rp.op_off + start;
         l.rt = rt;
         if (rt) {
-            l.rb = (S > 1 && h.opt_rb_multi) ? h.opt_rb_multi : sweep_reg_bits(S);
+            // pass-specialised multi-state passes hold 16 amplitudes per state and
+            // thread (more work per instruction stream, registers for early phi loads)
+            l.rb = (S > 1 && h.opt_rb_multi) ? h.opt_rb_multi : (S > 1 && use_jit) ? 4 : sweep_reg_bits(S);
             ProgInfo pi = build_program(dops, rp.op_off + start, rp.n_ops - start, l.rb, tab, prog);
             l.prog_index = pi.words_begin;
             l.args.prog_words = pi.n_words;
@@ -652,6 +655,8 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
     B.ti.build(m, level);
 
     B.rt = plan.k == kMaxTileQ;
+    B.use_jit = want_jit && B.rt && jit_available();
+    if (want_jit && B.rt && !B.use_jit) E.jit_state = -1;   // NVRTC missing: the interpreting kernel runs
     // finisher factor table (complex128)
     B.tab.kmats.assign((size_t)std::max(N, 1) * 32, 0.0);
     for (int s = 0; s < N; ++s)
@@ -887,7 +892,7 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
         return NQS_ERR_UNSUPPORTED;
     }
     // pass-specialised kernels for the register-resident passes
-    if (want_jit && B.rt) {
+    if (B.use_jit) {
         std::vector<JitPass*> todo;
         std::vector<Launch*> owner;
         for (auto& l : B.L) {

@@ -32,6 +32,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <set>
 #include <mutex>
 #include <sstream>
 #include <string>
@@ -158,6 +159,15 @@ static __device__ __forceinline__ float warp_rs8(const float (&w)[8], int lane) 
 )PRELUDE";
 
 // ------------------------------------------------------------------ code generation
+bool flush_rt_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = std::getenv("NQS_JIT_FLUSH");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
 std::string flit(float v) {
     char buf[64];
     if (v == 0.f) return std::signbit(v) ? "-0.0f" : "0.0f";
@@ -196,6 +206,15 @@ struct Gen {
     bool rp[4] = {};
     std::vector<cd> T;
     int tmp = 0;
+    std::set<int> early_phi;   // reductions of the current phase whose phi is loaded at the phase start
+
+    // reductions per phase whose phi values may be held in registers from the
+    // phase start: the 16-amplitude layouts have the registers, the 8-amplitude
+    // three-state layout (128 registers per thread) does not
+    int early_phi_budget() const {
+        if (const char* e = std::getenv("NQS_JIT_EARLY_PHI")) return std::atoi(e);
+        return (RB >= 4 && S > 1) ? 2 : 0;
+    }
 
     explicit Gen(const JitPass& j) : J(j) {
         S = J.S;
@@ -211,6 +230,8 @@ struct Gen {
     void reset_pending() {
         cs = 1.0;
         rs = false;
+        rs_new.clear();
+        for (auto& v : rp_new) v.clear();
         for (int i = 0; i < 4; ++i) {
             cp[i][0] = cp[i][1] = 1.0;
             rp[i] = false;
@@ -329,18 +350,31 @@ struct Gen {
         }
         std::fill(T.begin(), T.end(), cd(1.0));
     }
-    void flush_all() {
+    // Apply the pending diagonal to the amplitudes.  keep_scalar: a constant
+    // scalar (the same for every amplitude of every thread) stays pending --
+    // it survives re-layouts and is absorbed later by a dense gate, a spawn
+    // factor or the reduced matrix at no per-amplitude cost.
+    void flush_all(bool keep_scalar = false) {
+        const cd kept = keep_scalar ? cs : cd(1.0);
+        if (keep_scalar) cs = 1.0;
+        flush_now();
+        cs = kept;
+    }
+    // consts: also apply the compile-time part (else it stays pending)
+    void flush_now(bool consts = true) {
+        materialize();
         // constant part per amplitude and run-time part over the run-time pairs
         std::vector<int> rbits;
         for (int i = 0; i < RB; ++i)
             if (rp[i]) rbits.push_back(i);
         const bool any_rt = rs || !rbits.empty();
-        std::vector<cd> C(E);
-        for (int r = 0; r < E; ++r) {
-            cd c = cs * T[r];
-            for (int i = 0; i < RB; ++i) c *= cp[i][r >> i & 1];
-            C[r] = c;
-        }
+        std::vector<cd> C(E, cd(1.0));
+        if (consts)
+            for (int r = 0; r < E; ++r) {
+                cd c = cs * T[r];
+                for (int i = 0; i < RB; ++i) c *= cp[i][r >> i & 1];
+                C[r] = c;
+            }
         if (!any_rt) {
             for (int r = 0; r < E; ++r) {
                 if (is_one(C[r])) continue;
@@ -384,25 +418,81 @@ struct Gen {
             for (int s = 0; s < S; ++s)
                 o << "    x[" << s << "][" << r << "] = mulR(" << f << ", x[" << s << "][" << r << "]);\n";
         }
-        reset_pending();
+        if (consts) {
+            reset_pending();
+        } else {
+            rs = false;
+            for (int i = 0; i < 4; ++i) rp[i] = false;
+        }
     }
-    void scalar_mul_rt(const std::string& v) {
-        if (!rs) {
-            o << "    dsc = " << v << ";\n";
+    // Before a dense gate that would take run-time diagonal factors into its
+    // matrix: when two or more dense gates up to the next site would do so,
+    // multiply the run-time factors into the amplitudes once instead, so the
+    // gates keep constant (and often structured: real or imaginary) entries.
+    void maybe_flush_rt(int oi, int end) {
+        if (!(rs_pending() || rt_pending(0) || rt_pending(1) || rt_pending(2) || rt_pending(3))) return;
+        int k = 0;
+        bool scalar = rs_pending();
+        for (int j = oi; j < end; ++j) {
+            const OpRec& op = J.ops[j];
+            if (op.type == 5) break;
+            if (op.type == 1) {
+                if (scalar || rt_pending(op.la)) ++k;
+                scalar = false;
+            } else if (op.type == 2) {
+                if (scalar || rt_pending(op.la) || rt_pending(op.lb)) ++k;
+                scalar = false;
+            }
+        }
+        if (k >= 2) flush_now(false);
+    }
+    // Run-time factors are collected and multiplied as balanced product trees
+    // when first needed (short dependency chains instead of one serial chain
+    // through an accumulator).
+    std::vector<std::string> rs_new;                       // scalar factors not yet in dsc
+    std::vector<std::pair<std::string, std::string>> rp_new[4];
+    std::string tree(std::vector<std::string> v) {
+        while (v.size() > 1) {
+            std::vector<std::string> nx;
+            for (size_t k = 0; k + 1 < v.size(); k += 2) {
+                const std::string t = name("t");
+                o << "    const float2 " << t << " = mulR(" << v[k] << ", " << v[k + 1] << ");\n";
+                nx.push_back(t);
+            }
+            if (v.size() & 1) nx.push_back(v.back());
+            v.swap(nx);
+        }
+        return v.empty() ? "" : v[0];
+    }
+    void materialize() {
+        if (!rs_new.empty()) {
+            if (rs) rs_new.push_back("dsc");
+            const std::string t = tree(rs_new);
+            o << "    dsc = " << t << ";\n";
+            rs_new.clear();
             rs = true;
-        } else {
-            o << "    dsc = mulR(dsc, " << v << ");\n";
         }
-    }
-    void pair_mul_rt(int i, const std::string& v0, const std::string& v1) {
-        if (!rp[i]) {
-            o << "    dh" << i << "_0 = " << v0 << "; dh" << i << "_1 = " << v1 << ";\n";
+        for (int i = 0; i < 4; ++i) {
+            if (rp_new[i].empty()) continue;
+            std::vector<std::string> a, b;
+            for (auto& pr : rp_new[i]) {
+                a.push_back(pr.first);
+                b.push_back(pr.second);
+            }
+            if (rp[i]) {
+                a.push_back("dh" + std::to_string(i) + "_0");
+                b.push_back("dh" + std::to_string(i) + "_1");
+            }
+            const std::string ta = tree(a), tb = tree(b);
+            o << "    dh" << i << "_0 = " << ta << "; dh" << i << "_1 = " << tb << ";\n";
+            rp_new[i].clear();
             rp[i] = true;
-        } else {
-            o << "    dh" << i << "_0 = mulR(dh" << i << "_0, " << v0 << "); dh" << i << "_1 = mulR(dh" << i << "_1, "
-              << v1 << ");\n";
         }
     }
+    bool rt_pending(int i) const { return rp[i] || !rp_new[i].empty(); }
+    bool rs_pending() const { return rs || !rs_new.empty(); }
+    void scalar_mul_rt(const std::string& v) { rs_new.push_back(v); }
+    void pair_mul_rt(int i, const std::string& v0, const std::string& v1) { rp_new[i].push_back({v0, v1}); }
     static std::string c2(cd c) {
         const Cf f = to_cf(c);
         return "make_float2(" + flit(f.re) + ", " + flit(f.im) + ")";
@@ -411,6 +501,7 @@ struct Gen {
     // ---- operations ---------------------------------------------------------
     // run-time column factor rho_c of a dense gate: scalar times run-time pairs
     std::string column_rt(const std::vector<std::pair<int, int>>& bits) {
+        materialize();
         std::vector<std::string> fs;
         if (rs) fs.push_back("dsc");
         for (auto& ib : bits)
@@ -551,7 +642,8 @@ struct Gen {
     }
 
     void op_site(const OpRec& op, const cd* m, int phase_idx) {
-        flush_all();
+        flush_all(true);
+        const cd sc = cs;   // pending constant scalar: folded into what the site writes or reduces
         const int i = op.la;
         const int fl = op.flags;
         const DevPhase& d = J.phases[phase_idx];
@@ -563,12 +655,19 @@ struct Gen {
             const std::string p = save ? ("P.ckpt[" + std::to_string(op.site) + "]")
                                        : ("P.ckpt_fwd[" + std::to_string(op.site) + "]");
             o << "    float2* const sv = " << p << " + gb;\n";
-            emit_scatter("sv", [&](int r) { return "x[0][" + std::to_string(r) + "]"; });
+            emit_scatter("sv", [&](int r) {
+                const std::string v = "x[0][" + std::to_string(r) + "]";
+                return is_one(sc) ? v : "mulK(" + kargs(sc) + ", " + v + ")";
+            });
         }
         if (red) {
-            o << "    float2 ph[" << E << "];\n";
-            o << "    const float2* const pp = phi" << (int)op.ev << " + gb;\n";
-            emit_gather("ph", "pp", true);
+            if (early_phi.count(op.ev)) {
+                o << "    const float2 (&ph)[" << E << "] = phe" << (int)op.ev << ";\n";
+            } else {
+                o << "    float2 ph[" << E << "];\n";
+                o << "    const float2* const pp = phi" << (int)op.ev << " + gb;\n";
+                emit_gather("ph", "pp", true);
+            }
             for (int s = 0; s < S; ++s) {
                 o << "    { float2 R00 = make_float2(0.f, 0.f), R01 = R00, R10 = R00, R11 = R00;\n";
                 for (int r = 0; r < E; ++r) {
@@ -578,6 +677,9 @@ struct Gen {
                       << "], x[" << s << "][" << r1 << "], R01); R10 = cjfma(ph[" << r1 << "], x[" << s << "][" << r
                       << "], R10); R11 = cjfma(ph[" << r1 << "], x[" << s << "][" << r1 << "], R11);\n";
                 }
+                if (!is_one(sc))
+                    o << "      R00 = mulK(" << kargs(sc) << ", R00); R01 = mulK(" << kargs(sc) << ", R01); R10 = mulK("
+                      << kargs(sc) << ", R10); R11 = mulK(" << kargs(sc) << ", R11);\n";
                 o << "      const float w[8] = {R00.x, R00.y, R01.x, R01.y, R10.x, R10.y, R11.x, R11.y};\n";
                 o << "      const float v = warp_rs8(w, lane);\n";
                 o << "      if ((lane & 3) == 0) acc[((" << (int)op.ev << " * " << S << " + " << s << ") * " << NW
@@ -589,7 +691,8 @@ struct Gen {
             const int ns = op.nspawn;
             for (int s = 0; s < S; ++s)
                 for (int k = 0; k < ns; ++k) {
-                    const cd* K = m + 4 * (k + 1);
+                    const cd K[4] = {m[4 * (k + 1)] * sc, m[4 * (k + 1) + 1] * sc, m[4 * (k + 1) + 2] * sc,
+                                     m[4 * (k + 1) + 3] * sc};
                     o << "    { float2* const dp = P.spawn[" << s * 3 + k << "] + gb;\n";
                     // value of amplitude r of K x: rows by the site's bit
                     emit_scatter("dp", [&](int r) {
@@ -704,12 +807,30 @@ struct Gen {
                 o << "    __syncthreads();\n";
             }
             const DevPhase& d = J.phases[p];
+            // the phi values of this phase's reductions are loaded at the start
+            // of the phase (when the registers allow), so their latency overlaps
+            // the phase's gates
+            early_phi.clear();
+            if (early_phi_budget() > 0) {
+                int budget = early_phi_budget();
+                for (int oi = d.op_begin; oi < d.op_end && budget > 0; ++oi) {
+                    const OpRec& op = J.ops[oi];
+                    if (op.type != 5 || !(op.flags & 1)) continue;
+                    early_phi.insert(op.ev);
+                    --budget;
+                    o << "    float2 phe" << (int)op.ev << "[" << E << "];\n";
+                    o << "    { const float2* const pp = phi" << (int)op.ev << " + (b | gT" << p << ");\n";
+                    emit_gather("phe" + std::to_string((int)op.ev), "pp", true);
+                    o << "    }\n";
+                }
+            }
             for (int oi = d.op_begin; oi < d.op_end; ++oi) {
                 const OpRec& op = J.ops[oi];
                 cd m[16];
                 const int cnt = (op.type == 2 || op.type == 4 || (op.type == 5 && (op.flags & 2))) ? 16 : 4;
                 for (int e = 0; e < cnt; ++e) m[e] = mat(op.mat + e);
                 o << "    // op " << oi << " type " << (int)op.type << "\n";
+                if ((op.type == 1 || op.type == 2) && flush_rt_enabled()) maybe_flush_rt(oi, d.op_end);
                 switch (op.type) {
                     case 1: op_g1(op.la, m); break;
                     case 2: op_g2(op.la, op.lb, m); break;
@@ -719,7 +840,7 @@ struct Gen {
                     default: break;
                 }
             }
-            flush_all();
+            flush_all(p + 1 < n_ph);
         }
         // store the tile
         o << "    {\n";
