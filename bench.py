@@ -12,13 +12,16 @@ Printed JSON keys beyond the basic contract:
                    CUDA-event duration (events recorded by the library on the
                    launching stream during the timed steps), against the
                    measured HBM copy bandwidth;
-  cpu_baseline  -- the FP64 oracle (literal Algorithm 1, two state-vector
-                   contractions per term) timed on the host cores on a bounded
-                   sample of one term's contraction, scaled to terms/s;
+  cpu_baseline  -- the FP64 oracle O3 (forward/backward checkpoints, C/OpenMP)
+                   on the host cores: the first state passes of its complete
+                   call on this workload at full width, timed, scaled by the
+                   exact pass count of the call; plus O3's complete call on
+                   the 20-qubit grid workload and the one-sweep-per-term
+                   oracle's rate as labelled side fields;
   e2e           -- the same metric through the public C ABI from host data:
                    circuit text parsed, noise factored, schedule uploaded,
                    result read back to pageable host memory, every step.
---impl reference times the oracle alone (the reference arm).
+--impl reference times O3 alone, on the same config (the reference arm).
 """
 
 import argparse
@@ -191,6 +194,69 @@ def oracle_sample(w, level, target_s=12.0, max_ops=None):
                                     len(sample.arity))}
 
 
+def o3_sample(w, level, target_s=12.0, max_passes=None):
+    """Time O3 (the FP64 forward/backward-checkpoint oracle, C/OpenMP) on the
+    workload itself at full width: the first P state passes of its complete
+    call (v = U|psi>, backward checkpoints, depth-first forward sweep, both
+    networks of every term) run for real; the complete call's pass count T
+    is counted exactly.  terms/s = terms * (P / T) / seconds -- every pass
+    sweeps the whole state, so the sample's rate per pass is the call's."""
+    import workloads as W
+    from oracle import csim, o3
+    from oracle import ir as OIR
+    from oracle.expansion import term_count
+    c = OIR.parse(W.to_ir_text(w))
+    n_terms = term_count(len(c.noises), level)
+    v_bits = w.v["bits"] if w.v["kind"] == "basis" else -1
+    if max_passes is None:
+        # calibrate on 4 passes, then as many as fit in target_s
+        d0, total, t0 = o3.timed_sample(c, w.psi["bits"], v_bits, level, 4)
+        max_passes = max(4, min(total, int(target_s / max(t0 / d0, 1e-6))))
+    done, total, dt = o3.timed_sample(c, w.psi["bits"], v_bits, level, max_passes)
+    units = n_terms * done / total
+    return {"value": units / dt, "unit": "terms/s", "cores": csim.lib().nqso_num_threads(), "kind": "oracle",
+            "units": units, "seconds": dt, "passes": done, "passes_total": total,
+            "sample": "O3 (FP64 forward/backward checkpoints, C/OpenMP) on this workload at full width: the "
+                      "first %d of the %d state passes of its complete call (both networks of every term) "
+                      "timed, %.1f s; terms/s = %d terms x %d/%d / %.1f s" % (done, total, dt, n_terms, done,
+                                                                              total, dt)}
+
+
+def o3_full_call_c2():
+    """O3's complete call on the 20-qubit grid workload (1771 level-2 terms),
+    timed end to end: the oracle's whole-call rate on a workload it finishes."""
+    import workloads as W
+    from oracle import csim, o3
+    from oracle import ir as OIR
+    w = W.c2_grid20()
+    c = OIR.parse(W.to_ir_text(w))
+    t0 = time.perf_counter()
+    r = o3.approximate(c, w.psi, w.v, 2)
+    dt = time.perf_counter() - t0
+    return {"value": r["n_terms"] / dt, "unit": "terms/s", "seconds": dt, "terms": r["n_terms"],
+            "cores": csim.lib().nqso_num_threads(),
+            "workload": "grid20_l2 (4x5 grid depth 16, 20 AD*PD, level 2), complete call"}
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def workload_config(args, w, level, desc, n_terms):
+    return {"workload": args.workload, "description": desc, "n_qubits": w.n, "gates": len(w.gates),
+            "noises": w.n_noise, "level": level, "terms": n_terms, "state_bytes": 8 << w.n,
+            "l2": "inputs larger than L2 (8 GiB states)" if w.n >= 25 else "L2-resident states (no flush)",
+            "parallelism": "replicas" if dist_env()[0] > 1 else "single"}
+
+
 # ----------------------------------------------------------------------------- distributed
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -214,30 +280,38 @@ def aggregate(local_time, local_units, backend_device=None):
 
 # ----------------------------------------------------------------------------- arms
 def run_reference(args):
+    """The reference arm: the FP64 oracle O3 on the host cores, on the same
+    workload and config as the GPU arm.  Each step is a bounded part of O3's
+    complete call at full width (its first state passes, run for real); the
+    units of a step are the call's terms times the fraction of the call's
+    passes it ran, so value = units / time and ms_per_step is the measured
+    time of a step."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
     w, level, desc = make_workload(args.workload)
     if isinstance(w, list):
-        # many circuits: the oracle's rate on the largest one stands for the set
-        w = max(w, key=lambda c: (c.n, len(c.gates)))
-        level = w.levels[0]
-        desc += "; oracle timed on the widest circuit of the set"
-    vals = []
-    for i in range(args.warmup + args.steps):
-        r = oracle_sample(w, level, target_s=4.0)
-        if i >= args.warmup:
-            vals.append(r)
-    v = sum(x["value"] for x in vals) / len(vals)
-    from oracle import csim
+        return print(json.dumps({"impl": "reference", "unavailable": "the batch workload has no single-call "
+                                 "oracle timing; the oracle arm covers the single-circuit workloads"})) or 0
     from oracle.expansion import term_count
     n_terms = term_count(w.n_noise, level)
+    probe = o3_sample(w, level, target_s=4.0)
+    passes = probe["passes"]
+    units, secs, last = 0.0, 0.0, None
+    for i in range(args.warmup + args.steps):
+        r = o3_sample(w, level, max_passes=passes)
+        if i >= args.warmup:
+            units += r["units"]
+            secs += r["seconds"]
+            last = r
+    v = units / secs
+    from oracle import csim
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "terms/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * n_terms / v if v else None,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": {"workload": args.workload, "description": desc},
+            "data": "synthetic", "config": workload_config(args, w, level, desc, n_terms),
             "cpu_baseline": {"value": v, "unit": "terms/s", "cores": csim.lib().nqso_num_threads(),
-                             "kind": "oracle", "sample": vals[-1]["sample"]},
+                             "cpu": cpu_model(), "kind": "oracle", "sample": last["sample"]},
             "e2e": {"value": v, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -354,7 +428,10 @@ def run_nqs(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            cpu = oracle_sample(w, level)
+            cpu = o3_sample(w, level)
+            cpu["cpu"] = cpu_model()
+            cpu["full_call"] = o3_full_call_c2()
+            cpu["literal_per_term"] = oracle_sample(w, level, target_s=3.0)
         except Exception as ex:  # the baseline must never sink the GPU measurement
             cpu = {"value": None, "unit": "terms/s", "cores": os.cpu_count(), "kind": "oracle",
                    "sample": "failed: %s" % ex}
@@ -364,11 +441,7 @@ def run_nqs(args):
             "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": {"workload": args.workload, "description": desc, "n_qubits": w.n,
-                       "gates": len(w.gates), "noises": w.n_noise, "level": level, "terms": n_terms,
-                       "state_bytes": 8 << w.n, "l2": "inputs larger than L2 (8 GiB states)" if w.n >= 25
-                       else "L2-resident states (no flush)",
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": workload_config(args, w, level, desc, n_terms),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if peak else None, "traffic": traffic,
                          "kernel": dom_name, "peak_source": peak_src,

@@ -190,7 +190,8 @@ int nqs_get_info(nqs_handle h, nqs_info* out);
 /* Launch list of the handle's current schedule (the one the last
  * nqs_fidelity call built), for profiling: one record per launch, in launch
  * order.  kind: 0 sweep pass, 1 finisher, 2 state fill, 3 state copy,
- * 4 two-state reduction, 5 level sums.  For sweep passes: states swept
+ * 4 two-state reduction, 5 level sums, 6 normalisation of the computed
+ * v = U|psi> (basis psi).  For sweep passes: states swept
  * together, register qubits per thread (0: shared-memory tile kernel), phases
  * of the register-resident program, grid size, operation counts
  * ops[] = {dense 1-qubit, dense 2-qubit, diagonal 1-qubit, diagonal 2-qubit,
@@ -294,18 +295,22 @@ size_t nqs_reduced_matrix_scratch_bytes(int n);
  * NQS_NOALLOC_MAX_BLOCKS * 8 doubles (64 KiB) compiled into the library;
  * every GPU that loads the library holds it until the process exits.  The
  * call allocates nothing: no cudaMalloc, no cudaFree, no allocator callback.
- *   - phi, chi: device, 2^n complex64 each, 16-byte aligned; n in 1..NQS_NOALLOC_MAX_QUBITS.
- *   - R_out: device-accessible memory (device, managed or pinned host),
+ *   - phi, chi: memory of the current device (or managed), 2^n complex64
+ *     each, 16-byte aligned; n in 1..NQS_NOALLOC_MAX_QUBITS.  Host memory
+ *     and another device's memory are rejected with NQS_ERR_ARG.
+ *   - R_out: the current device's memory, managed or pinned host memory,
  *     8-byte aligned; written by a kernel in `stream`.  Pageable host
  *     memory is rejected with NQS_ERR_ARG.
+ *   - stream: NULL or a stream of the current device (NQS_ERR_ARG otherwise).
  *   - The first call on each device resolves the array's device address
  *     (cudaGetSymbolAddress) with that device current and caches it.
  *   - Every call on a device shares the one array and overwrites the
  *     slots it reads, so sequential calls need no clearing; calls whose
  *     kernels overlap on the GPU (different streams, no ordering between
  *     them) race on the array and must be serialised by the caller.
- * Errors: NQS_ERR_ARG (NULL, misaligned, qubit >= n, pageable R_out),
- * NQS_ERR_TOO_LARGE (n > NQS_NOALLOC_MAX_QUBITS), NQS_ERR_CUDA. */
+ * Errors: NQS_ERR_ARG (NULL, misaligned, qubit >= n, a pointer or stream
+ * the current device cannot use), NQS_ERR_TOO_LARGE (n > NQS_NOALLOC_MAX_QUBITS),
+ * NQS_ERR_CUDA. */
 #define NQS_NOALLOC_MAX_BLOCKS 1024
 #define NQS_NOALLOC_MAX_QUBITS 34
 int nqs_reduced_matrix_noalloc(const void* phi, const void* chi, int n, int qubit, double* R_out, void* stream);

@@ -33,9 +33,11 @@
  * for narrow ones (n <= 16) the first insertions (s, j) are spread over the
  * threads, each with its own work states.
  */
+#define _POSIX_C_SOURCE 199309L
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -442,4 +444,286 @@ int64_t nqso3_term_count(int n_sites, const int* m, int level) {
     free(o.set_off);
     free(o.binom);
     return t;
+}
+
+/* ------------------------------------------------------------------ chosen site sets */
+
+/* Sweep w from event e0 through the sites of set c[depth..k-1]: gates and the
+ * dominant factor at every site not in the set; at site c[depth] every
+ * non-dominant factor is inserted in turn (depth first); at the last site the
+ * reduced matrix against phi gives all its factors at once.  amps receives
+ * prod(m - 1) values per set in lexicographic factor order. */
+static void set_expand(const O3* o, cplx* w, int e0, const int* c, int k, int depth, cplx** bufs, cplx* out,
+                       int64_t* pos, int par) {
+    const int64_t dim = (int64_t)1 << o->n;
+    const int target = c[depth];
+    const int et = o->site_ev[target];
+    for (int e = e0; e < et; ++e) {
+        const int nq = o->nq[e], q0 = o->q0[e], q1 = o->q1[e];
+        if (o->kind[e] == 0) apply(o->n, w, nq, q0, q1, o->mat + (size_t)e * 16, 0, par);
+        else apply(o->n, w, nq, q0, q1, factor(o, o->site[e], 0), 0, par);
+    }
+    const int nq = o->nq[et], q0 = o->q0[et], q1 = o->q1[et];
+    if (depth == k - 1) {
+        cplx R[16];
+        reduced(o->n, o->phi[target], w, nq, q0, q1, R, par);
+        for (int j = 1; j < o->m[target]; ++j) out[(*pos)++] = contract(factor(o, target, j), R, nq == 1 ? 2 : 4);
+        return;
+    }
+    for (int j = 1; j < o->m[target]; ++j) {
+        cplx* w2 = bufs[depth + 1];
+        memcpy(w2, w, (size_t)dim * sizeof(cplx));
+        apply(o->n, w2, nq, q0, q1, factor(o, target, j), 0, par);
+        set_expand(o, w2, et + 1, c, k, depth + 1, bufs, out, pos, par);
+    }
+}
+
+/*
+ * Amplitudes of every factor choice on each of m_sets chosen site sets
+ * (k sites each, ascending), the dominant factor at all other sites: for set
+ * S the prod_{s in S}(m_s - 1) amplitudes in lexicographic factor order, sets
+ * one after the other.  Same network arguments as nqso3_amplitudes.  Returns
+ * 0, or -1 (bad argument / out of memory).
+ */
+int nqso3_set_amplitudes(int n, int n_ev, const int* kind, const int* nq, const int* q0, const int* q1,
+                         const int* site, const double* mat, int n_sites, const int* m, const double* fac,
+                         const double* psi, const double* bra, int k, const int* sets, int64_t m_sets,
+                         double* amps, int threads) {
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#else
+    (void)threads;
+#endif
+    if (n < 1 || n > 40 || k < 1 || k > 8 || n_sites < k || !amps) return -1;
+    O3 o;
+    memset(&o, 0, sizeof o);
+    o.n = n; o.n_ev = n_ev; o.kind = kind; o.nq = nq; o.q0 = q0; o.q1 = q1; o.site = site;
+    o.mat = (const cplx*)mat; o.n_sites = n_sites; o.m = m; o.fac = (const cplx*)fac;
+    const int64_t dim = (int64_t)1 << n;
+    int rc = 0;
+    o.site_ev = (int*)calloc((size_t)n_sites, sizeof(int));
+    for (int e = 0; e < n_ev; ++e)
+        if (kind[e] == 1) {
+            if (site[e] < 0 || site[e] >= n_sites) { free(o.site_ev); return -1; }
+            o.site_ev[site[e]] = e;
+        }
+    for (int64_t a = 0; a < m_sets; ++a)
+        for (int j = 0; j < k; ++j) {
+            const int s = sets[a * k + j];
+            if (s < 0 || s >= n_sites || (j > 0 && s <= sets[a * k + j - 1])) { free(o.site_ev); return -1; }
+        }
+    /* backward checkpoints for every site, forward ones where a set starts */
+    o.phi = (cplx**)calloc((size_t)n_sites, sizeof(cplx*));
+    cplx** chi = (cplx**)calloc((size_t)n_sites, sizeof(cplx*));
+    char* first = (char*)calloc((size_t)n_sites, 1);
+    for (int64_t a = 0; a < m_sets; ++a) first[sets[a * k]] = 1;
+    cplx** bufs = (cplx**)calloc((size_t)k, sizeof(cplx*));
+    cplx* p = new_state(n);
+    if (!p) { rc = -1; goto done; }
+    memcpy(p, bra, (size_t)dim * sizeof(cplx));
+    for (int e = n_ev - 1; e >= 0; --e) {
+        if (kind[e] == 0) {
+            apply(n, p, nq[e], q0[e], q1[e], o.mat + (size_t)e * 16, 1, 1);
+        } else {
+            const int t = site[e];
+            o.phi[t] = new_state(n);
+            if (!o.phi[t]) { rc = -1; goto done; }
+            memcpy(o.phi[t], p, (size_t)dim * sizeof(cplx));
+            apply(n, p, nq[e], q0[e], q1[e], factor(&o, t, 0), 1, 1);
+        }
+    }
+    memcpy(p, psi, (size_t)dim * sizeof(cplx));
+    for (int e = 0; e < n_ev; ++e) {
+        if (kind[e] == 0) {
+            apply(n, p, nq[e], q0[e], q1[e], o.mat + (size_t)e * 16, 0, 1);
+        } else {
+            const int t = site[e];
+            if (first[t]) {
+                chi[t] = new_state(n);
+                if (!chi[t]) { rc = -1; goto done; }
+                memcpy(chi[t], p, (size_t)dim * sizeof(cplx));
+            }
+            apply(n, p, nq[e], q0[e], q1[e], factor(&o, t, 0), 0, 1);
+        }
+    }
+    for (int j = 0; j < k; ++j) {
+        bufs[j] = new_state(n);
+        if (!bufs[j]) { rc = -1; goto done; }
+    }
+    {
+        int64_t pos = 0;
+        for (int64_t a = 0; a < m_sets; ++a) {
+            const int* c = sets + a * k;
+            memcpy(bufs[0], chi[c[0]], (size_t)dim * sizeof(cplx));
+            set_expand(&o, bufs[0], o.site_ev[c[0]], c, k, 0, bufs, (cplx*)amps, &pos, 1);
+        }
+    }
+done:
+    free(p);
+    for (int t = 0; t < n_sites; ++t) {
+        if (o.phi) free(o.phi[t]);
+        free(chi[t]);
+    }
+    free(o.phi);
+    free(chi);
+    free(first);
+    for (int j = 0; j < k; ++j) free(bufs[j]);
+    free(bufs);
+    free(o.site_ev);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ timing a bounded part of a call */
+
+/* A pass budget: at most `max` state passes (one application of an operation,
+ * a reduction or a state copy, each a sweep over 2^n amplitudes); `dry` only
+ * counts them, touching no state. */
+typedef struct {
+    int64_t max, done;
+    int dry, stop;
+} Budget;
+
+static int take(Budget* b) {
+    if (b->stop) return 0;
+    if (b->done >= b->max) {
+        b->stop = 1;
+        return 0;
+    }
+    b->done++;
+    return !b->dry;
+}
+
+static double now_s(void) {
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
+/* A state for the timed call, its pages touched at once (zeroed) and the time
+ * that takes added to *excluded: the first touch of fresh memory is paid once
+ * per state of a complete call, which a short sample would overweight. */
+static cplx* new_state_touched(int n, double* excluded) {
+    const double t0 = now_s();
+    cplx* p = new_state(n);
+    if (p) memset(p, 0, ((size_t)1 << n) * sizeof(cplx));
+    *excluded += now_s() - t0;
+    return p;
+}
+
+/* expand() of the wide-state call, pass by pass under a budget */
+static void expand_budget(const O3* o, cplx* w, int e0, int depth, Bufs* B, Budget* bu) {
+    const int64_t dim = (int64_t)1 << o->n;
+    for (int e = e0; e <= o->last_site_ev; ++e) {
+        if (bu->stop) return;
+        const int nq = o->nq[e], q0 = o->q0[e], q1 = o->q1[e];
+        if (o->kind[e] == 0) {
+            if (take(bu)) apply(o->n, w, nq, q0, q1, o->mat + (size_t)e * 16, 0, 1);
+            continue;
+        }
+        const int t = o->site[e];
+        const int last0 = depth == 0 && e == o->last_site_ev;
+        if (depth < o->level || last0) {
+            cplx R[16];
+            if (take(bu)) reduced(o->n, o->phi[t], w, nq, q0, q1, R, 1);
+            if (depth < o->level)
+                for (int j = 1; j < o->m[t] && depth + 1 < o->level; ++j) {
+                    cplx* w2 = B->work[depth + 1];
+                    if (take(bu)) memcpy(w2, w, (size_t)dim * sizeof(cplx));
+                    if (take(bu)) apply(o->n, w2, nq, q0, q1, factor(o, t, j), 0, 1);
+                    expand_budget(o, w2, e + 1, depth + 1, B, bu);
+                    if (bu->stop) return;
+                }
+        }
+        if (take(bu)) apply(o->n, w, nq, q0, q1, factor(o, t, 0), 0, 1);
+    }
+}
+
+/*
+ * The wide-state (n > 16) path of nqso3_amplitudes -- psi = |psi_bits>, the
+ * bra given, or |v_bits> (v_bits >= 0), or v = U|psi> computed first
+ * (v_bits < 0), backward checkpoints, then
+ * the depth-first forward sweep -- executed pass by pass until `max_passes`
+ * passes are done (amplitudes are not kept), or, with dry = 1, only counted.
+ * Returns the passes executed (or counted) and, in *seconds, their time (the
+ * allocation and first touch of each state excluded); the caller scales by
+ * the pass count of the complete call.  Returns -1 when a state cannot be
+ * allocated.
+ */
+int64_t nqso3_timed_passes(int n, int n_ev, const int* kind, const int* nq, const int* q0, const int* q1,
+                           const int* site, const double* mat, int n_sites, const int* m, const double* fac,
+                           int64_t psi_bits, int64_t v_bits, const double* bra, int level, int64_t max_passes,
+                           int dry, double* seconds, int threads) {
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#else
+    (void)threads;
+#endif
+    if (n < 1 || n > 40 || level < 0 || n_sites < 1) return -1;
+    if (level > n_sites) level = n_sites;
+    O3 o;
+    memset(&o, 0, sizeof o);
+    o.n = n; o.n_ev = n_ev; o.kind = kind; o.nq = nq; o.q0 = q0; o.q1 = q1; o.site = site;
+    o.mat = (const cplx*)mat; o.n_sites = n_sites; o.m = m; o.fac = (const cplx*)fac; o.level = level;
+    const int64_t dim = (int64_t)1 << n;
+    for (int e = 0; e < n_ev; ++e)
+        if (kind[e] == 1) o.last_site_ev = e;
+    Budget bu = {max_passes, 0, dry, 0};
+    int64_t rc = 0;
+    double excluded = 0.0;
+    const double t_start = now_s();
+    cplx* psi = dry ? NULL : new_state_touched(n, &excluded);
+    cplx* v = dry ? NULL : new_state_touched(n, &excluded);
+    cplx* p = dry ? NULL : new_state_touched(n, &excluded);
+    Bufs B;
+    B.work = (cplx**)calloc((size_t)level + 1, sizeof(cplx*));
+    o.phi = (cplx**)calloc((size_t)n_sites, sizeof(cplx*));
+    if (!dry && (!psi || !v || !p)) { rc = -1; goto done; }
+    if (take(&bu)) {   /* |psi_bits> */
+        memset(psi, 0, (size_t)dim * sizeof(cplx));
+        psi[psi_bits].re = 1.0;
+    }
+    if (bra) {
+        if (take(&bu)) memcpy(v, bra, (size_t)dim * sizeof(cplx));
+    } else if (v_bits >= 0) {
+        if (take(&bu)) {
+            memset(v, 0, (size_t)dim * sizeof(cplx));
+            v[v_bits].re = 1.0;
+        }
+    } else {           /* v = U |psi> */
+        if (take(&bu)) memcpy(v, psi, (size_t)dim * sizeof(cplx));
+        for (int e = 0; e < n_ev && !bu.stop; ++e)
+            if (kind[e] == 0 && take(&bu)) apply(n, v, nq[e], q0[e], q1[e], o.mat + (size_t)e * 16, 0, 1);
+    }
+    if (take(&bu)) memcpy(p, v, (size_t)dim * sizeof(cplx));
+    for (int e = n_ev - 1; e >= 0 && !bu.stop; --e) {
+        if (kind[e] == 0) {
+            if (take(&bu)) apply(n, p, nq[e], q0[e], q1[e], o.mat + (size_t)e * 16, 1, 1);
+        } else {
+            const int t = site[e];
+            if (!dry && !bu.stop) {
+                o.phi[t] = new_state_touched(n, &excluded);
+                if (!o.phi[t]) { rc = -1; goto done; }
+            }
+            if (take(&bu)) memcpy(o.phi[t], p, (size_t)dim * sizeof(cplx));
+            if (take(&bu)) apply(n, p, nq[e], q0[e], q1[e], factor(&o, t, 0), 1, 1);
+        }
+    }
+    if (!dry && !bu.stop)
+        for (int dd = 0; dd <= level; ++dd) {
+            B.work[dd] = new_state_touched(n, &excluded);
+            if (!B.work[dd]) { rc = -1; goto done; }
+        }
+    if (take(&bu)) memcpy(B.work[0], psi, (size_t)dim * sizeof(cplx));
+    expand_budget(&o, B.work[0], 0, 0, &B, &bu);
+    rc = bu.done;
+    if (seconds) *seconds = now_s() - t_start - excluded;
+done:
+    free(psi);
+    free(v);
+    free(p);
+    for (int dd = 0; dd <= level; ++dd) free(B.work[dd]);
+    free(B.work);
+    for (int t = 0; t < n_sites; ++t) free(o.phi[t]);
+    free(o.phi);
+    return rc;
 }

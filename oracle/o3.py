@@ -52,6 +52,13 @@ def lib():
         L.nqso3_amplitudes.argtypes = [ctypes.c_int, ctypes.c_int, ip, ip, ip, ip, ip, dp, ctypes.c_int, ip, dp,
                                        dp, dp, ctypes.c_int, dp, ctypes.c_int64, P(ctypes.c_int64), ctypes.c_int]
         L.nqso3_amplitudes.restype = ctypes.c_int
+        L.nqso3_set_amplitudes.argtypes = [ctypes.c_int, ctypes.c_int, ip, ip, ip, ip, ip, dp, ctypes.c_int, ip,
+                                           dp, dp, dp, ctypes.c_int, ip, ctypes.c_int64, dp, ctypes.c_int]
+        L.nqso3_set_amplitudes.restype = ctypes.c_int
+        L.nqso3_timed_passes.argtypes = [ctypes.c_int, ctypes.c_int, ip, ip, ip, ip, ip, dp, ctypes.c_int, ip, dp,
+                                         ctypes.c_int64, ctypes.c_int64, dp, ctypes.c_int, ctypes.c_int64,
+                                         ctypes.c_int, P(ctypes.c_double), ctypes.c_int]
+        L.nqso3_timed_passes.restype = ctypes.c_int64
         L.nqso3_term_count.argtypes = [ctypes.c_int, ip, ctypes.c_int]
         L.nqso3_term_count.restype = ctypes.c_int64
         _lib = L
@@ -121,6 +128,53 @@ class Network:
         return out
 
 
+    def set_amplitudes(self, psi, bra, sets, threads=0):
+        """For each chosen site set (rows of `sets`, ascending sites) the
+        amplitudes of every choice of non-dominant factors at its sites, the
+        dominant factor elsewhere: a list of arrays in lexicographic order."""
+        sets = np.ascontiguousarray(np.asarray(sets, dtype=np.int32))
+        m_sets, k = sets.shape
+        per = [int(np.prod([self.m[s] - 1 for s in row])) for row in sets]
+        out = np.zeros(sum(per), np.complex128)
+        mat = np.ascontiguousarray(self.mat).view(np.float64)
+        fac = np.ascontiguousarray(self.fac).view(np.float64)
+        psi = np.ascontiguousarray(psi, np.complex128)
+        bra = np.ascontiguousarray(bra, np.complex128)
+        rc = lib().nqso3_set_amplitudes(self.n, len(self.kind), _ip(self.kind), _ip(self.nq), _ip(self.q0),
+                                        _ip(self.q1), _ip(self.site), _dp(mat), len(self.m), _ip(self.m), _dp(fac),
+                                        _dp(psi.view(np.float64)), _dp(bra.view(np.float64)), k, _ip(sets), m_sets,
+                                        _dp(out.view(np.float64)), threads)
+        if rc != 0:
+            raise RuntimeError("O3 set amplitudes failed (%d)" % rc)
+        res, off = [], 0
+        for c in per:
+            res.append(out[off:off + c])
+            off += c
+        return res
+
+
+    def passes(self, psi_bits, v_bits, bra, level, max_passes, dry, threads=0):
+        """State passes of this network's wide-state call (see
+        nqso3_timed_passes): executed up to max_passes, or only counted.
+        bra=None: the bra is |v_bits>, or v = U|psi_bits> when v_bits < 0."""
+        mat = np.ascontiguousarray(self.mat).view(np.float64)
+        fac = np.ascontiguousarray(self.fac).view(np.float64)
+        if bra is None:
+            bp = None
+        else:
+            bra = np.ascontiguousarray(bra, np.complex128)
+            bp = _dp(bra.view(np.float64))
+        secs = ctypes.c_double(0.0)
+        r = lib().nqso3_timed_passes(self.n, len(self.kind), _ip(self.kind), _ip(self.nq), _ip(self.q0),
+                                     _ip(self.q1), _ip(self.site), _dp(mat), len(self.m), _ip(self.m), _dp(fac),
+                                     int(psi_bits), int(v_bits), bp, level, int(max_passes), 1 if dry else 0,
+                                     ctypes.byref(secs), threads)
+        if r < 0:
+            raise MemoryError("O3: a state does not fit in host memory")
+        self.last_seconds = secs.value
+        return int(r)
+
+
 def networks(circuit, factors=None):
     """The two networks of Algorithm 1 for a parsed circuit: (gates U, factors
     U_i) and (gates U^*, factors V_i), factors from expansion.svd_factors."""
@@ -181,3 +235,32 @@ def approximate(circuit, psi_spec, v_spec, level, threads=0, factors=None):
     x = a * b
     T = level_sums(x, len(circuit.noises), level, na.m)
     return {"F": sum(T), "T": T, "terms": x, "n_terms": len(x)}
+
+
+def set_weights(circuit, psi_spec, v_spec, sets, threads=0, factors=None):
+    """W(S) = sum over the factor choices at the sites of S of X = a * b
+    (Sec. IV: the level-|S| terms of one site set), for each row of `sets`."""
+    n = circuit.n
+    psi = state_from_spec(psi_spec, n)
+    v = state_from_spec(v_spec, n, circuit, psi)
+    na, nb = networks(circuit, factors)
+    a = na.set_amplitudes(psi, v, sets, threads)
+    b = nb.set_amplitudes(psi.conj(), v.conj(), sets, threads)
+    return np.array([complex(np.sum(x * y)) for x, y in zip(a, b)])
+
+
+def timed_sample(circuit, psi_bits, v_bits, level, max_passes, threads=0):
+    """Time the first `max_passes` state passes of O3's complete call
+    (psi = |psi_bits>, v = |v_bits> or, for v_bits < 0, U|psi> computed in C;
+    both networks), and count
+    the passes of the complete call.  Returns (passes_done, passes_total,
+    seconds of those passes, allocation and first touch of states excluded):
+    the call's time is seconds * passes_total / passes_done when every pass
+    sweeps the full state, as here."""
+    na, nb = networks(circuit)
+    level = min(level, len(circuit.noises))
+    dummy = np.zeros(1, np.complex128)
+    total = (na.passes(psi_bits, v_bits, None, level, 1 << 62, True) +
+             nb.passes(psi_bits, v_bits, dummy, level, 1 << 62, True) + 1)
+    done = na.passes(psi_bits, v_bits, None, level, max_passes, False, threads)
+    return done, total, na.last_seconds

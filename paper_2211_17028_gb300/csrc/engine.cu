@@ -800,6 +800,23 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
                 l.src = pp;
                 B.L.push_back(l);
             }
+            if (psi->kind == NQS_STATE_BASIS && !B.run_ideal.passes.empty()) {
+                // U|psi> has the norm of the basis state, 1: restore it (the
+                // complex64 gates lose a little; v enters every term twice)
+                Launch r;
+                r.kind = L_REDUCE2;
+                r.src = mainb;
+                r.dst = mainb;
+                r.bits = 0;
+                r.grid = std::max(1, std::min<int>(E.sm_count * 4, (int)std::max<long long>(1, B.dim / (2 * kThreads * 16))));
+                B.partial_doubles = std::max(B.partial_doubles, (size_t)r.grid * 8);
+                B.L.push_back(r);
+                Launch nl;
+                nl.kind = L_NORMALIZE;
+                nl.dst = mainb;
+                nl.fin_grid = r.grid;
+                B.L.push_back(nl);
+            }
         } else {
             init_state(v, mainb, ext, ext_ptr);
         }
@@ -1043,6 +1060,8 @@ int run_launch(Handle& h, Engine& E, const Launch& l, cudaStream_t st) {
         case L_SUM:
             return cuda_err(launch_level_sum(E.term_vals, E.level_off_dev, E.eff_level, E.res_dev, E.bound, E.n_terms,
                                              E.err_dev, st));
+        case L_NORMALIZE:
+            return cuda_err(launch_normalize(l.dst, dim, E.partials, l.fin_grid, fill_grid, st));
     }
     return NQS_ERR_ARG;
 }

@@ -7,6 +7,7 @@
 #include <memory>
 #include <vector>
 
+#include "fp32_round.h"
 #include "jit.h"
 #include "nqs_internal.h"
 #include "sweep_types.h"
@@ -29,7 +30,7 @@ struct Run {
     std::vector<RunPass> passes;     // in execution order
 };
 
-enum LaunchKind { L_PASS, L_FINISH, L_FILL, L_COPY, L_REDUCE2, L_SUM };
+enum LaunchKind { L_PASS, L_FINISH, L_FILL, L_COPY, L_REDUCE2, L_SUM, L_NORMALIZE };
 
 struct Launch {
     LaunchKind kind;
@@ -103,13 +104,15 @@ struct Engine {
 struct Tables {
     std::vector<float2> mats;
     std::vector<double> kmats;     // per site: K_0..K_3, 8 doubles each
+    // unitary matrices are rounded to stay as unitary as FP32 allows (fp32_round.h)
     int add(const cd* m, int cnt, bool adjoint, int dim) {
         int off = (int)mats.size();
+        cd v[16];
         for (int r = 0; r < dim; ++r)
-            for (int c = 0; c < dim; ++c) {
-                cd v = adjoint ? std::conj(m[dim * c + r]) : m[dim * r + c];
-                mats.push_back(make_float2((float)v.real(), (float)v.imag()));
-            }
+            for (int c = 0; c < dim; ++c) v[dim * r + c] = adjoint ? std::conj(m[dim * c + r]) : m[dim * r + c];
+        float2 f[16];
+        round_matrix_c64(v, dim, f);
+        for (int e = 0; e < dim * dim; ++e) mats.push_back(f[e]);
         (void)cnt;
         return off;
     }

@@ -39,6 +39,7 @@
 #include <thread>
 #include <vector>
 
+#include "fp32_round.h"
 #include "jit.h"
 
 namespace nqs {
@@ -178,7 +179,10 @@ std::string flit(float v) {
 struct Cf {   // complex constant rounded to float
     float re, im;
 };
-Cf to_cf(cd c) { return Cf{(float)c.real(), (float)c.imag()}; }
+Cf to_cf(cd c) {
+    const float2 f = round_c64(c);   // unit-modulus constants stay as close to the unit circle as FP32 allows
+    return Cf{f.x, f.y};
+}
 bool is_one(cd c) {
     const Cf f = to_cf(c);
     return f.re == 1.f && f.im == 0.f;
@@ -498,6 +502,14 @@ struct Gen {
         return "make_float2(" + flit(f.re) + ", " + flit(f.im) + ")";
     }
 
+    // the FP32 matrix closest to unitary (when the exact one is), returned as the
+    // doubles of those floats so the emitters print them unchanged
+    static void round_matrix(cd* K, int dim) {
+        float2 f[16];
+        round_matrix_c64(K, dim, f);
+        for (int e = 0; e < dim * dim; ++e) K[e] = cd(f[e].x, f[e].y);
+    }
+
     // ---- operations ---------------------------------------------------------
     // run-time column factor rho_c of a dense gate: scalar times run-time pairs
     std::string column_rt(const std::vector<std::pair<int, int>>& bits) {
@@ -523,6 +535,7 @@ struct Gen {
         for (int c = 0; c < 2; ++c) rho[c] = column_rt({{i, c}});
         for (int rr = 0; rr < 2; ++rr)
             for (int c = 0; c < 2; ++c) K[2 * rr + c] = m[2 * rr + c] * cs * cp[i][c];
+        round_matrix(K, 2);
         const bool rt = !rho[0].empty() || !rho[1].empty();
         std::string mv[4];
         if (rt) {
@@ -563,6 +576,7 @@ struct Gen {
         for (int c = 0; c < 4; ++c) rho[c] = column_rt({{i0, c >> 1}, {i1, c & 1}});
         for (int q = 0; q < 4; ++q)
             for (int c = 0; c < 4; ++c) K[4 * q + c] = m[4 * q + c] * cs * cp[i0][c >> 1] * cp[i1][c & 1];
+        round_matrix(K, 4);
         bool rt = false;
         for (int c = 0; c < 4; ++c) rt = rt || !rho[c].empty();
         std::string mv[16];

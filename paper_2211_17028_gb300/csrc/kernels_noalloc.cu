@@ -49,6 +49,22 @@ int scratch_address(double** out) {
     return NQS_OK;
 }
 
+// Memory a kernel on device `dev` may use: device memory of that device,
+// managed memory, or (when allowed, for the result) pinned host memory.
+int check_pointer(const void* p, int dev, bool pinned_host_ok) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return NQS_ERR_ARG;
+    }
+    switch (a.type) {
+        case cudaMemoryTypeDevice: return a.device == dev ? NQS_OK : NQS_ERR_ARG;
+        case cudaMemoryTypeManaged: return NQS_OK;
+        case cudaMemoryTypeHost: return pinned_host_ok ? NQS_OK : NQS_ERR_ARG;
+        default: return NQS_ERR_ARG;   // pageable host memory
+    }
+}
+
 }  // namespace
 
 }  // namespace nqs
@@ -59,18 +75,26 @@ extern "C" int nqs_reduced_matrix_noalloc(const void* phi, const void* chi, int 
     if (!phi || !chi || !R_out || n < 1 || qubit < 0 || qubit >= n) return NQS_ERR_ARG;
     if (n > NQS_NOALLOC_MAX_QUBITS) return NQS_ERR_TOO_LARGE;
     if (((uintptr_t)phi & 15u) || ((uintptr_t)chi & 15u) || ((uintptr_t)R_out & 7u)) return NQS_ERR_ARG;
-    // R_out is written by a kernel: it must be device-accessible memory
-    cudaPointerAttributes attr;
-    if (cudaPointerGetAttributes(&attr, R_out) != cudaSuccess) {
-        cudaGetLastError();
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return NQS_ERR_CUDA;
+    // the kernels run on the current device: the states must live there (or
+    // be managed), the result may also be pinned host memory, and the stream
+    // must belong to that device (the cached scratch address is this device's)
+    if (check_pointer(phi, dev, false) != NQS_OK || check_pointer(chi, dev, false) != NQS_OK ||
+        check_pointer(R_out, dev, true) != NQS_OK)
         return NQS_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (st) {
+        int sdev = -1;
+        if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) {
+            cudaGetLastError();
+            return NQS_ERR_ARG;
+        }
+        if (sdev != dev) return NQS_ERR_ARG;
     }
-    if (attr.type == cudaMemoryTypeUnregistered) return NQS_ERR_ARG;
     double* scratch = nullptr;
     int rc = scratch_address(&scratch);
     if (rc != NQS_OK) return rc;
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return NQS_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return NQS_ERR_CUDA;
     // same grid rule as nqs_reduced_matrix (about 16 pairs per thread per
     // round, at most 4 blocks per SM), capped by the scratch capacity
@@ -80,7 +104,6 @@ extern "C" int nqs_reduced_matrix_noalloc(const void* phi, const void* chi, int 
     g = std::min<long long>(g, 2048);
     g = std::min<long long>(g, NQS_NOALLOC_MAX_BLOCKS);
     const int grid = (int)std::max<long long>(1, g);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     // every block overwrites its 8 partial slots before the sum reads them,
     // so nothing left by an earlier call is read
     if (launch_reduce2x2((const float2*)phi, (const float2*)chi, n, qubit, scratch, grid, st) != cudaSuccess)

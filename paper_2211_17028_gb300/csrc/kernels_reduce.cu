@@ -229,6 +229,33 @@ cudaError_t launch_finish(const double* partials, int grid, const FinishDesc* de
     return cudaGetLastError();
 }
 
+// v <- v / ||v||, the norm from the per-block partials of reduce2x2_kernel(v,
+// v, qubit 0): ||v||^2 = Re R00 + Re R11, summed in a fixed order by every
+// block.  The noiseless circuit keeps the norm of a basis state, 1; complex64
+// gates lose a little of it, and v enters F twice.
+__global__ void __launch_bounds__(kThreads) normalize_kernel(float2* __restrict__ v, long long dim,
+                                                             const double* __restrict__ part, int grid) {
+    __shared__ float scale;
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int g = 0; g < grid; ++g) a += part[(size_t)g * 8] + part[(size_t)g * 8 + 6];
+        scale = a > 0.0 ? (float)(1.0 / sqrt(a)) : 1.0f;
+    }
+    __syncthreads();
+    const float f = scale;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride) {
+        const float2 x = v[i];
+        v[i] = make_float2(x.x * f, x.y * f);
+    }
+}
+
+cudaError_t launch_normalize(float2* v, long long dim, const double* partials, int red_grid, int grid,
+                             cudaStream_t st) {
+    normalize_kernel<<<grid, kThreads, 0, st>>>(v, dim, partials, red_grid);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_partials_sum(const double* part, int grid, double* R, cudaStream_t st) {
     partials_sum_kernel<<<1, kThreads, 0, st>>>(part, grid, R);
     return cudaGetLastError();

@@ -150,6 +150,8 @@ cudaError_t launch_reduce2x2(const float2* phi, const float2* chi, int n, int q,
 cudaError_t launch_finish(const double* partials, int grid, const FinishDesc* desc, const double* kmats,
                           double* vals, int n_red, cudaStream_t st);
 cudaError_t launch_partials_sum(const double* part, int grid, double* R, cudaStream_t st);
+cudaError_t launch_normalize(float2* v, long long dim, const double* partials, int red_grid, int grid,
+                             cudaStream_t st);
 cudaError_t launch_level_sum(const double* vals, const long long* level_off, int level, nqs_result* res,
                              double bound, long long n_terms, const int* err, cudaStream_t st);
 cudaError_t launch_basis_fill(float2* out, long long dim, unsigned long long bits, int grid, cudaStream_t st);

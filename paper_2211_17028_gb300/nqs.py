@@ -350,7 +350,7 @@ def nqs_get_info(h):
     return {f: getattr(info, f) for f, _ in nqs_info._fields_}
 
 
-LAUNCH_KINDS = ("pass", "finish", "fill", "copy", "reduce2", "sum")
+LAUNCH_KINDS = ("pass", "finish", "fill", "copy", "reduce2", "sum", "normalize")
 OP_COUNT_NAMES = ("g1", "g2", "d1", "d2", "sites", "reductions", "spawned", "saves")
 
 

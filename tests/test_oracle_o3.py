@@ -117,3 +117,44 @@ def test_o3_term_count_and_order():
     # level 2: sets (0,1),(0,2),(0,3),(1,2),(1,3): (1,3) starts at 10+3+6+9+2 = 30, idx (1,2) -> +1
     assert list(nz) == [0, 4, 8, 31]
     assert np.allclose(amps[nz], [1, 2, 3, 6])
+
+
+@pytest.mark.parametrize("seed,n,k", [(51, 6, 1), (52, 5, 2), (53, 7, 3), (54, 17, 2)])
+def test_o3_set_weights_equal_the_full_list(seed, n, k):
+    # W(S) of chosen sets = the full level-k list summed per site set
+    w = W.random_circuit(seed, n, 30 if n < 10 else 20, 6 if n < 10 else 4, rate_lo=1e-2, rate_hi=5e-2,
+                         v_kind="ideal")
+    c = _circ(w)
+    r = O3.approximate(c, w.psi, w.v, k)
+    N = len(c.noises)
+    recs = EX.enumerate_records(N, k)
+    sums = {}
+    for rec, x in zip(recs, r["terms"]):
+        u = rec & 15
+        if u != k:
+            continue
+        key = tuple(((rec >> (4 + 14 * j)) & 0xFFF) for j in range(u))
+        sums[key] = sums.get(key, 0) + x
+    import itertools
+    sets = list(itertools.combinations(range(N), k))[::2]
+    got = O3.set_weights(c, w.psi, w.v, np.array(sets))
+    want = np.array([sums[tuple(s)] for s in sets])
+    assert np.max(np.abs(got - want)) <= 1e-13 * max(1e-300, np.max(np.abs(want))) + 1e-300
+
+
+def test_o3_timed_sample_predicts_the_complete_call():
+    # the CPU baseline's method: the first passes of O3's call, timed and scaled
+    # by the call's exact pass count, must predict the complete call's time
+    import time
+    w = W.qaoa_workload(17, 3, 8, 2, "ideal", "qaoa17")
+    c = _circ(w)
+    t0 = time.perf_counter()
+    O3.approximate(c, w.psi, w.v, 2)
+    full = time.perf_counter() - t0
+    done, total, secs = O3.timed_sample(c, 0, -1, 2, 400)
+    assert 0 < done <= total
+    pred = secs * total / done
+    assert 0.4 * full < pred < 2.5 * full, (pred, full)
+    # and the pass count is that of the call: counting twice gives the same
+    d2, t2, _ = O3.timed_sample(c, 0, -1, 2, 1)
+    assert t2 == total and d2 == 1
