@@ -146,7 +146,7 @@ def test_o3_timed_sample_predicts_the_complete_call():
     # the CPU baseline's method: the first passes of O3's call, timed and scaled
     # by the call's exact pass count, must predict the complete call's time
     import time
-    w = W.qaoa_workload(17, 3, 8, 2, "ideal", "qaoa17")
+    w = W.qaoa_workload(18, 3, 8, 2, "ideal", "qaoa18")
     c = _circ(w)
     t0 = time.perf_counter()
     O3.approximate(c, w.psi, w.v, 2)
