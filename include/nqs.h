@@ -169,6 +169,39 @@ int nqs_term_values(nqs_handle h, double* out, size_t cap, size_t* count);
  * dropped and dominant parts, Theorem 1's argument per site). */
 int nqs_truncation_bound(nqs_handle h, int level, double* out);
 
+/* Adaptive level selection (Theorem 1 and the level study of Sec. V: the
+ * truncation error falls with the level, and a low level usually suffices).
+ * The level is raised until the dropped part is below `tol`, judged by
+ *   NQS_ADAPT_BOUND     the truncation bound (nqs_truncation_bound): the
+ *                       smallest level l with bound(l) <= tol is evaluated
+ *                       directly -- the bound needs only the factors' norms;
+ *   NQS_ADAPT_OBSERVED  the last level's sum: levels 1, 2, ... are evaluated
+ *                       in turn until |T_l| <= tol (the next terms are
+ *                       smaller still for weak noise, as the paper observes);
+ *   both flags          whichever stops first.
+ * Levels never exceed max_level (nor N).  `out` (host memory) receives the
+ * result of the last evaluated level, out->level that level.  The call
+ * synchronises `stream` after each evaluated level (it reads T_l).
+ * Errors: as nqs_fidelity; NQS_ERR_ARG for tol < 0, max_level < 0 or no
+ * criterion flag. */
+enum { NQS_ADAPT_BOUND = 1, NQS_ADAPT_OBSERVED = 2 };
+
+/* One element <x| E(|psi><psi|) |y> of the output density matrix at level l
+ * (Sec. III: every element can be estimated on its own, by the identity
+ *   <x|rho|y> = 1/4 [ f(x+y) - f(x-y) - i f(x+iy) + i f(x-iy) ],
+ * f(v) = <v|rho|v>).  The level-l approximation is <v|rho_l|v> for one
+ * Hermitian rho_l, so the identity holds level by level: four level-l calls
+ * with v = x + i^k y (dense, built on the device) and their combination.
+ *   x, y: NQS_STATE_BASIS or NQS_STATE_DENSE (not IDEAL).
+ *   out: host, 2 doubles (re, im).  parts: NULL or host array of 4 results,
+ *        the calls for k = 0..3.
+ * One temporary state (8 * 2^n bytes) comes from the allocator; the call
+ * synchronises `stream`.  Errors: as nqs_fidelity. */
+int nqs_offdiagonal(nqs_handle h, const nqs_state* psi, const nqs_state* x, const nqs_state* y, int level,
+                    double* out, nqs_result* parts, void* stream);
+int nqs_fidelity_adaptive(nqs_handle h, const nqs_state* psi, const nqs_state* v, double tol, int max_level,
+                          uint32_t criteria, nqs_result* out, void* stream);
+
 typedef struct {
     int32_t n_qubits;
     int32_t n_gates;

@@ -64,6 +64,19 @@ def final_density_matrix(circuit, psi_vec):
     return rho
 
 
+def matrix_element(circuit, psi_spec, x_spec, y_spec):
+    """<x| E(|psi><psi|) |y>, one element of the output density matrix
+    (Sec. III: every element can be estimated on its own)."""
+    n = circuit.n
+    if n > 12:
+        raise ValueError("density-matrix oracle limited to n <= 12")
+    psi = state_from_spec(psi_spec, n)
+    x = state_from_spec(x_spec, n, circuit, psi)
+    y = state_from_spec(y_spec, n, circuit, psi)
+    rho = final_density_matrix(circuit, psi)
+    return complex(np.vdot(x, rho @ y))
+
+
 def fidelity(circuit, psi_spec, v_spec):
     """Exact F = <v| E(|psi><psi|) |v> (Problem 1)."""
     n = circuit.n

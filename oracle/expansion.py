@@ -188,6 +188,35 @@ def approximate(circuit, psi_spec, v_spec, level, keep_terms=False, amplitude_fn
             "n_terms": term_count(n_noise, level)}
 
 
+def approximate_offdiagonal(circuit, psi_spec, x_spec, y_spec, level):
+    """Level-l approximation of one element <x| E(|psi><psi|) |y> (Sec. III).
+
+    The double-size network of Sec. III ends in <x| on the original wires and
+    <y^*| on the conjugate wires; substituting the factors of Sec. IV and
+    keeping the assignments of Algorithm 1 gives, per kept assignment, the
+    product of the original-side network with bra <x| and the conjugate-side
+    network with bra <y^*|.  For x = y this is approximate()."""
+    n = circuit.n
+    psi = state_from_spec(psi_spec, n)
+    x = state_from_spec(x_spec, n, circuit, psi)
+    y = state_from_spec(y_spec, n, circuit, psi)
+    factors = prepared_factors(circuit)
+    n_noise = len(circuit.noises)
+    level = min(level, n_noise)
+    per_level = [[] for _ in range(level + 1)]
+    for k, sites, idx in kept_assignments(n_noise, level):
+        choice = [0] * n_noise
+        for s, i in zip(sites, idx):
+            choice[s] = i
+        ins_u = [factors[s][1][choice[s]] for s in range(n_noise)]
+        ins_v = [factors[s][2][choice[s]] for s in range(n_noise)]
+        a = _network_amplitude(circuit, psi, x, ins_u, False)
+        b = _network_amplitude(circuit, psi, y, ins_v, True)
+        per_level[k].append(a * b)
+    t = [_fsum_complex(xs) for xs in per_level]
+    return {"value": _fsum_complex(t), "T": t, "n_terms": term_count(n_noise, level)}
+
+
 def site_set_sums(terms, n_noise):
     """Sum of term values per site set (basis independent under degenerate
     singular values).  terms: [(record, X)]."""

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -243,6 +244,89 @@ int nqs_truncation_bound(nqs_handle hh, int level, double* out) {
     double b = 0.0;
     for (size_t i = (size_t)level + 1; i < poly.size(); ++i) b += poly[i];
     *out = b;
+    return NQS_OK;
+}
+
+int nqs_fidelity_adaptive(nqs_handle hh, const nqs_state* psi, const nqs_state* v, double tol, int max_level,
+                          uint32_t criteria, nqs_result* out, void* stream) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !out || !(tol >= 0.0) || max_level < 0) return NQS_ERR_ARG;
+    if (!(criteria & (NQS_ADAPT_BOUND | NQS_ADAPT_OBSERVED)) || (criteria & ~3u)) return NQS_ERR_ARG;
+    if (!h->prepared) return NQS_ERR_ORDER;
+    const int N = (int)h->factors.size();
+    int top = std::min(std::min(max_level, N), NQS_MAX_LEVEL);
+    if (criteria & NQS_ADAPT_BOUND) {
+        // smallest level whose truncation bound is within tol
+        int l = 0;
+        double b = 0.0;
+        for (; l < top; ++l) {
+            if (nqs_truncation_bound(hh, l, &b) != NQS_OK) return NQS_ERR_ARG;
+            if (b <= tol) break;
+        }
+        top = l;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int start = (criteria & NQS_ADAPT_OBSERVED) ? std::min(1, top) : top;
+    for (int l = start; l <= top; ++l) {
+        int rc = nqs_fidelity(hh, psi, v, l, out, stream);
+        if (rc != NQS_OK) return rc;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return NQS_ERR_CUDA;
+        if (out->status != NQS_OK) return NQS_OK;   // the device error is in out->status
+        if ((criteria & NQS_ADAPT_OBSERVED) && std::fabs(out->T[l]) <= tol) break;
+    }
+    return NQS_OK;
+}
+
+int nqs_offdiagonal(nqs_handle hh, const nqs_state* psi, const nqs_state* x, const nqs_state* y, int level,
+                    double* out, nqs_result* parts, void* stream) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !out || level < 0) return NQS_ERR_ARG;
+    if (!h->prepared) return NQS_ERR_ORDER;
+    int rc = check_state(*h, psi, false);
+    if (rc) return rc;
+    if (check_state(*h, x, false) || check_state(*h, y, false)) return NQS_ERR_ARG;
+    const int lvl = std::min(level, (int)h->factors.size());
+    if (lvl > NQS_MAX_LEVEL) return NQS_ERR_ARG;
+    const long long dim = 1ll << h->circ.n;
+    const size_t bytes = (size_t)dim * 8;
+    cudaStream_t st = (cudaStream_t)stream;
+    float2* v = (float2*)dev_alloc(bytes, stream);
+    if (!v) return NQS_ERR_NOMEM;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * 8, dim / 256));
+    // f(v) = <v|rho_l|v> for v = x + i^k y, k = 0..3;  <x|rho_l|y> = 1/4 sum_k i^(-k) f(x + i^k y)
+    const float cr[4] = {1.f, 0.f, -1.f, 0.f}, ci[4] = {0.f, 1.f, 0.f, -1.f};
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < 4 && rc == NQS_OK; ++k) {
+        if (launch_combine(v, dim, x->kind == NQS_STATE_DENSE, x->bits, (const float2*)x->dev,
+                           y->kind == NQS_STATE_DENSE, y->bits, (const float2*)y->dev, cr[k], ci[k], grid,
+                           st) != cudaSuccess) {
+            rc = NQS_ERR_CUDA;
+            break;
+        }
+        nqs_state vs{};
+        vs.kind = NQS_STATE_DENSE;
+        vs.dev = v;
+        nqs_result r{};
+        rc = engine_fidelity(*h, psi, &vs, lvl, &r, stream);
+        if (rc == NQS_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = NQS_ERR_CUDA;
+        if (rc != NQS_OK) break;
+        if (parts) parts[k] = r;
+        if (r.status != NQS_OK) rc = r.status;
+        // i^(-k) f_k
+        const double f = r.F;
+        if (k == 0) re += f;
+        else if (k == 1) im -= f;
+        else if (k == 2) re -= f;
+        else im += f;
+    }
+    cudaStreamSynchronize(st);
+    dev_free(v, bytes, stream);
+    if (rc != NQS_OK) return rc;
+    out[0] = 0.25 * re;
+    out[1] = 0.25 * im;
     return NQS_OK;
 }
 

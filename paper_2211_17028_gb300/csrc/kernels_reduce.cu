@@ -256,6 +256,27 @@ cudaError_t launch_normalize(float2* v, long long dim, const double* partials, i
     return cudaGetLastError();
 }
 
+// out = x + c y for basis or dense x, y (the superposed states of the
+// polarization identity); a basis state is |bits> (kind 0), dense ones are
+// read from device memory (kind 1)
+__global__ void __launch_bounds__(kThreads) combine_kernel(float2* __restrict__ out, long long dim, int xk,
+                                                           unsigned long long xb, const float2* __restrict__ xd,
+                                                           int yk, unsigned long long yb,
+                                                           const float2* __restrict__ yd, float cre, float cim) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride) {
+        const float2 a = xk ? xd[i] : make_float2((unsigned long long)i == xb ? 1.f : 0.f, 0.f);
+        const float2 b = yk ? yd[i] : make_float2((unsigned long long)i == yb ? 1.f : 0.f, 0.f);
+        out[i] = make_float2(a.x + cre * b.x - cim * b.y, a.y + cre * b.y + cim * b.x);
+    }
+}
+
+cudaError_t launch_combine(float2* out, long long dim, int xk, unsigned long long xb, const float2* xd, int yk,
+                           unsigned long long yb, const float2* yd, float cre, float cim, int grid, cudaStream_t st) {
+    combine_kernel<<<grid, kThreads, 0, st>>>(out, dim, xk, xb, xd, yk, yb, yd, cre, cim);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_partials_sum(const double* part, int grid, double* R, cudaStream_t st) {
     partials_sum_kernel<<<1, kThreads, 0, st>>>(part, grid, R);
     return cudaGetLastError();

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "../../include/nqs.h"
 
 namespace nqs {
@@ -157,6 +159,9 @@ int selftest_bounded_wait(int* status, void* stream);
 int engine_reduced_matrix(const void* phi, const void* chi, int n, int qubit, double* R_out,
                           void* scratch, size_t scratch_bytes, void* stream);
 size_t engine_reduced_matrix_scratch_bytes(int n);
+// out = x + (cre + i cim) y on the device (kernels_reduce.cu); kind 1: dense, 0: |bits>
+cudaError_t launch_combine(float2* out, long long dim, int xk, unsigned long long xb, const float2* xd, int yk,
+                           unsigned long long yb, const float2* yd, float cre, float cim, int grid, cudaStream_t st);
 
 // proposal network (mlp.cu)
 struct Mlp;

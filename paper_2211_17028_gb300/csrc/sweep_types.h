@@ -152,6 +152,8 @@ cudaError_t launch_finish(const double* partials, int grid, const FinishDesc* de
 cudaError_t launch_partials_sum(const double* part, int grid, double* R, cudaStream_t st);
 cudaError_t launch_normalize(float2* v, long long dim, const double* partials, int red_grid, int grid,
                              cudaStream_t st);
+cudaError_t launch_combine(float2* out, long long dim, int xk, unsigned long long xb, const float2* xd, int yk,
+                           unsigned long long yb, const float2* yd, float cre, float cim, int grid, cudaStream_t st);
 cudaError_t launch_level_sum(const double* vals, const long long* level_off, int level, nqs_result* res,
                              double bound, long long n_terms, const int* err, cudaStream_t st);
 cudaError_t launch_basis_fill(float2* out, long long dim, unsigned long long bits, int grid, cudaStream_t st);

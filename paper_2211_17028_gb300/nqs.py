@@ -116,6 +116,12 @@ _SIGS = {
     "nqs_term_values": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t,
                                        ctypes.POINTER(ctypes.c_size_t)]),
     "nqs_truncation_bound": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "nqs_offdiagonal": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(nqs_state), ctypes.POINTER(nqs_state),
+                                       ctypes.POINTER(nqs_state), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(nqs_result), ctypes.c_void_p]),
+    "nqs_fidelity_adaptive": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(nqs_state), ctypes.POINTER(nqs_state),
+                                             ctypes.c_double, ctypes.c_int, ctypes.c_uint32,
+                                             ctypes.POINTER(nqs_result), ctypes.c_void_p]),
     "nqs_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(nqs_info)]),
     "nqs_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]),
     "nqs_selftest_bounded_wait": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
@@ -342,6 +348,33 @@ def nqs_truncation_bound(h, level):
     out = ctypes.c_double()
     _check(_lib().nqs_truncation_bound(h, level, ctypes.byref(out)), "nqs_truncation_bound")
     return out.value
+
+
+NQS_ADAPT_BOUND = 1
+NQS_ADAPT_OBSERVED = 2
+
+
+def nqs_fidelity_adaptive(h, psi, v, tol, max_level=NQS_MAX_LEVEL, criteria=NQS_ADAPT_BOUND | NQS_ADAPT_OBSERVED,
+                          stream=None):
+    """Raise the level until the truncation bound or the last level's sum is
+    within tol (synchronises the stream); the result of the level reached."""
+    ps, vs = _as_state(psi), _as_state(v)
+    out = nqs_result()
+    _check(_lib().nqs_fidelity_adaptive(h, ctypes.byref(ps), ctypes.byref(vs), float(tol), int(max_level),
+                                        int(criteria), ctypes.byref(out), _stream_ptr(stream)),
+           "nqs_fidelity_adaptive")
+    return out.to_dict()
+
+
+def nqs_offdiagonal(h, psi, x, y, level, stream=None):
+    """<x|rho_l|y> by the polarization identity (four level-l calls); returns
+    (complex value, [four result dicts])."""
+    ps, xs, ys = _as_state(psi), _as_state(x), _as_state(y)
+    out = (ctypes.c_double * 2)()
+    parts = (nqs_result * 4)()
+    _check(_lib().nqs_offdiagonal(h, ctypes.byref(ps), ctypes.byref(xs), ctypes.byref(ys), int(level), out, parts,
+                                  _stream_ptr(stream)), "nqs_offdiagonal")
+    return complex(out[0], out[1]), [parts[k].to_dict() for k in range(4)]
 
 
 def nqs_get_info(h):

@@ -603,3 +603,36 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(B, "theorem1_bound", good_t1)
     test_per_site_bound_identical_depolarizing_is_a_binomial_tail()
     test_theorem1_bound_hand_values()
+
+
+# ----------------------------------------------------------------------------
+# off-diagonal elements <x|rho|y> (Sec. III)
+
+@pytest.mark.parametrize("seed", [61, 62])
+def test_offdiagonal_full_level_is_the_density_matrix_element(seed):
+    w = W.random_circuit(seed, 3, 20, 3, rate_lo=1e-2, rate_hi=0.1)
+    c = _circ(w)
+    rng = _rng(seed)
+    x = {"kind": "dense", "amps": W.circuits.random_dense_state(rng, 3)}
+    y = {"kind": "basis", "bits": 5}
+    want = DM.matrix_element(c, w.psi, x, y)
+    got = EX.approximate_offdiagonal(c, w.psi, x, y, 3)["value"]
+    assert abs(got - want) < 1e-13
+    # Hermiticity of the level-l approximation and the x = y reduction
+    for lvl in (0, 1, 2):
+        a = EX.approximate_offdiagonal(c, w.psi, x, y, lvl)["value"]
+        b = EX.approximate_offdiagonal(c, w.psi, y, x, lvl)["value"]
+        assert abs(a - b.conjugate()) < 1e-14
+        assert abs(EX.approximate_offdiagonal(c, w.psi, x, x, lvl)["value"] -
+                   EX.approximate(c, w.psi, x, lvl)["F"]) < 1e-14
+
+
+def test_offdiagonal_basis_elements_of_a_known_state():
+    # identity circuit, one depolarizing noise on |+>: rho = (1-2p/3)|+><+| + (p/3) I ... element <0|rho|1>
+    # = (1 - 4p/3) / 2 for the paper-form channel (the coherence shrinks by 1 - 4p/3)
+    p = 0.09
+    w = W.identity_workload(1, [(0, ch.depolarizing_paper(p))])
+    w.psi = {"kind": "dense", "amps": [2 ** -0.5, 2 ** -0.5]}
+    c = _circ(w)
+    got = EX.approximate_offdiagonal(c, w.psi, {"kind": "basis", "bits": 0}, {"kind": "basis", "bits": 1}, 1)
+    assert abs(got["value"] - (1 - 4 * p / 3) / 2) < 1e-15
