@@ -106,7 +106,7 @@ def circuit_ops(circuit, inserted=None, conjugate=False, upto_event=None):
             g = G.gate_matrix(name, ps)
             ops.add(qs, g.conj() if conjugate else g)
         elif inserted is not None:
-            ops.add((circuit.noises[idx][1],), inserted[idx])
+            ops.add(IR.site_qubits(circuit.noises[idx][1]), inserted[idx])
     return ops
 
 

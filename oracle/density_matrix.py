@@ -10,6 +10,7 @@ import numpy as np
 
 from . import gates as G
 from . import ir as IR
+from . import ir as IR
 from . import statevector as SV
 
 
@@ -33,6 +34,26 @@ def apply_channel(rho, n, qubits, kraus):
     for e in kraus:
         acc += _left_right(rho, n, qubits, e, e)
     return acc
+
+
+def apply_superop(rho, n, qubits, m):
+    """rho -> the linear map whose matrix representation is M (Sec. III), on
+    `qubits`, by its definition: vec(rho')[(o, o')] = sum_{i, i'} M[(o, o'),
+    (i, i')] vec(rho)[(i, i')], where o, i index the site's qubits on the row
+    (original) side and o', i' on the column (conjugate) side, each as
+    2*b(q0) + b(q1).  For M = sum_k E_k (x) E_k^* this is sum_k E_k rho E_k^dagger."""
+    k = len(qubits)
+    t = rho.reshape((2,) * (2 * n))        # axis j: row qubit n-1-j; axis n+j: column qubit n-1-j
+    rows = [n - 1 - q for q in qubits]
+    cols = [2 * n - 1 - q for q in qubits]
+    mt = np.asarray(m).reshape((2,) * (4 * k))   # [o..., o'..., i..., i'...]
+    out = np.tensordot(mt, t, axes=(list(range(2 * k, 4 * k)), rows + cols))
+    # out axes: o (k), o' (k), then the remaining axes of t in order
+    rest = [a for a in range(2 * n) if a not in rows + cols]
+    order = rows + cols + rest
+    res = np.empty_like(t)
+    res = np.moveaxis(out, list(range(2 * k + len(rest))), order)
+    return res.reshape(rho.shape)
 
 
 def state_from_spec(spec, n, circuit=None, psi=None):
@@ -59,8 +80,11 @@ def final_density_matrix(circuit, psi_vec):
             u = G.gate_matrix(name, ps)
             rho = _left_right(rho, n, qs, u, u)
         else:
-            _, q, kraus = circuit.noises[idx]
-            rho = apply_channel(rho, n, (q,), kraus)
+            _, q, spec = circuit.noises[idx]
+            if isinstance(spec, IR.SuperOp):
+                rho = apply_superop(rho, n, IR.site_qubits(q), spec.m)
+            else:
+                rho = apply_channel(rho, n, IR.site_qubits(q), spec)
     return rho
 
 

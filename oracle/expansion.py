@@ -43,38 +43,49 @@ class NotDominant(ValueError):
 
 
 def matrix_representation(kraus):
-    """M_E = sum_k E_k (x) E_k^*  (Sec. III)."""
-    m = np.zeros((4, 4), dtype=np.complex128)
+    """M_E = sum_k E_k (x) E_k^*  (Sec. III); a d^2 x d^2 matrix for d x d
+    Kraus operators; a noise given as a SuperOp is its matrix already."""
+    if isinstance(kraus, IR.SuperOp):
+        return kraus.m.copy()
+    d = kraus[0].shape[0]
+    m = np.zeros((d * d, d * d), dtype=np.complex128)
     for e in kraus:
         m += np.kron(e, e.conj())
     return m
 
 
 def tensor_permutation(m):
-    """Regroup a 4x4 matrix with (row edges 1,2 ; column edges 3,4) into
-    (row edges 1,3 ; column edges 2,4)  (Sec. IV, Fig. 3a).  An involution."""
-    t = np.asarray(m).reshape(2, 2, 2, 2)          # [e1, e2, e3, e4]
-    return t.transpose(0, 2, 1, 3).reshape(4, 4)   # [(e1, e3), (e2, e4)]
+    """Regroup a d^2 x d^2 matrix with (row edges 1,2 ; column edges 3,4) into
+    (row edges 1,3 ; column edges 2,4)  (Sec. IV, Fig. 3a).  An involution.
+    Edge 1 is the original wire's output, 2 the conjugate wire's output, 3 and
+    4 their inputs; for a two-qubit noise every edge carries both qubits."""
+    m = np.asarray(m)
+    d = int(round(m.shape[0] ** 0.5))
+    t = m.reshape(d, d, d, d)                          # [e1, e2, e3, e4]
+    return t.transpose(0, 2, 1, 3).reshape(d * d, d * d)   # [(e1, e3), (e2, e4)]
 
 
 def svd_factors(kraus):
     """SVD of M~ and the factors of Fig. 3.
 
-    Returns (d, U, V, Ut, Vt): singular values d_0 >= ... >= d_3, 2x2 factors
+    Returns (d, U, V, Ut, Vt): singular values d_0 >= ... >= d_{m-1}
+    (m = 4 for a one-qubit noise, 16 for a two-qubit one), d x d factors
     with M_E = sum_i U_i (x) V_i, and the vectors U~_i = d_i S|i>, V~_i = T|i>.
     Raises NotDominant when d_0 does not strictly exceed d_1 (the dominant
     factor would not be unique)."""
     mt = tensor_permutation(matrix_representation(kraus))
+    m = mt.shape[0]
+    dd = int(round(m ** 0.5))
     s, d, th = np.linalg.svd(mt)
     t = th.conj().T
     if d[0] - d[1] <= DOMINANCE_RTOL * d[0]:
         raise NotDominant("largest singular value is not unique")
-    ut = [d[i] * s[:, i] for i in range(4)]
-    vt = [t[:, i] for i in range(4)]
+    ut = [d[i] * s[:, i] for i in range(m)]
+    vt = [t[:, i] for i in range(m)]
     # U~_i V~_i^dagger, permuted back, is U_i (x) V_i with
     # U_i[e1, e3] = U~_i[(e1, e3)] and V_i[e2, e4] = conj(V~_i[(e2, e4)])
-    u = [ut[i].reshape(2, 2) for i in range(4)]
-    v = [vt[i].conj().reshape(2, 2) for i in range(4)]
+    u = [ut[i].reshape(dd, dd) for i in range(m)]
+    v = [vt[i].conj().reshape(dd, dd) for i in range(m)]
     return d, u, v, ut, vt
 
 
@@ -82,19 +93,21 @@ def dominant_and_rest(kraus):
     """M' = U_0 (x) V_0 and M-bar = sum_{i>=1} U_i (x) V_i (Sec. IV)."""
     _, u, v, _, _ = svd_factors(kraus)
     m_dom = np.kron(u[0], v[0])
-    m_rest = sum(np.kron(u[i], v[i]) for i in range(1, 4))
+    m_rest = sum(np.kron(u[i], v[i]) for i in range(1, len(u)))
     return m_dom, m_rest
 
 
 # ----------------------------------------------------------------------------
 # kept assignments (O4)
 
-def kept_assignments(n_noise, level):
-    """(k, sites, factors) in Algorithm 1's loop order."""
+def kept_assignments(n_noise, level, m=None):
+    """(k, sites, factors) in Algorithm 1's loop order; m[s] factors at site s
+    (4 for every site when m is None), index 0 the dominant one."""
     level = min(level, n_noise)
     for k in range(level + 1):
         for sites in itertools.combinations(range(n_noise), k):
-            for idx in itertools.product((1, 2, 3), repeat=k):
+            ranges = [range(1, 4 if m is None else m[s]) for s in sites]
+            for idx in itertools.product(*ranges):
                 yield k, sites, idx
 
 
@@ -113,9 +126,11 @@ def enumerate_records(n_noise, level):
     return [pack_record(k, s, i) for k, s, i in kept_assignments(n_noise, level)]
 
 
-def term_count(n_noise, level):
+def term_count(n_noise, level, m=None):
     level = min(level, n_noise)
-    return sum(math.comb(n_noise, u) * 3 ** u for u in range(level + 1))
+    if m is None:
+        return sum(math.comb(n_noise, u) * 3 ** u for u in range(level + 1))
+    return sum(1 for _ in kept_assignments(n_noise, level, m))
 
 
 # ----------------------------------------------------------------------------
@@ -135,7 +150,7 @@ def _network_amplitude(circuit, psi, v, inserted, conjugate_side):
             g = G.gate_matrix(name, ps)
             s = SV.apply_op(s, n, qs, g.conj() if conjugate_side else g)
         else:
-            s = SV.apply_1q(s, n, circuit.noises[idx][1], inserted[idx])
+            s = SV.apply_op(s, n, IR.site_qubits(circuit.noises[idx][1]), inserted[idx])
     bra = v.conj() if conjugate_side else v
     return complex(np.vdot(bra, s))
 
@@ -173,19 +188,21 @@ def approximate(circuit, psi_spec, v_spec, level, keep_terms=False, amplitude_fn
     factors = prepared_factors(circuit)
     n_noise = len(circuit.noises)
     level = min(level, n_noise)
+    m = [len(f[1]) for f in factors]
     per_level = [[] for _ in range(level + 1)]
     terms = []
-    for k, sites, idx in kept_assignments(n_noise, level):
+    for k, sites, idx in kept_assignments(n_noise, level, m):
         if amplitude_fn is None:
             x = term_value(circuit, psi, v, factors, sites, idx)
         else:
             x = amplitude_fn(circuit, psi, v, factors, sites, idx)
         per_level[k].append(x)
         if keep_terms:
-            terms.append((pack_record(k, sites, idx) if k <= 4 else None, x))
+            packable = k <= 4 and all(i <= 3 for i in idx) and all(s < 4096 for s in sites)
+            terms.append((pack_record(k, sites, idx) if packable else None, x))
     t = [_fsum_complex(xs) for xs in per_level]
     return {"F": _fsum_complex(t), "T": t, "terms": terms,
-            "n_terms": term_count(n_noise, level)}
+            "n_terms": term_count(n_noise, level, m)}
 
 
 def approximate_offdiagonal(circuit, psi_spec, x_spec, y_spec, level):
@@ -203,8 +220,9 @@ def approximate_offdiagonal(circuit, psi_spec, x_spec, y_spec, level):
     factors = prepared_factors(circuit)
     n_noise = len(circuit.noises)
     level = min(level, n_noise)
+    m = [len(f[1]) for f in factors]
     per_level = [[] for _ in range(level + 1)]
-    for k, sites, idx in kept_assignments(n_noise, level):
+    for k, sites, idx in kept_assignments(n_noise, level, m):
         choice = [0] * n_noise
         for s, i in zip(sites, idx):
             choice[s] = i
@@ -214,7 +232,7 @@ def approximate_offdiagonal(circuit, psi_spec, x_spec, y_spec, level):
         b = _network_amplitude(circuit, psi, y, ins_v, True)
         per_level[k].append(a * b)
     t = [_fsum_complex(xs) for xs in per_level]
-    return {"value": _fsum_complex(t), "T": t, "n_terms": term_count(n_noise, level)}
+    return {"value": _fsum_complex(t), "T": t, "n_terms": term_count(n_noise, level, m)}
 
 
 def site_set_sums(terms, n_noise):

@@ -188,9 +188,9 @@ def networks(circuit, factors=None):
             ev_a.append(("gate", qs, g))
             ev_b.append(("gate", qs, g.conj()))
         else:
-            q = circuit.noises[idx][1]
-            ev_a.append(("site", idx, (q,)))
-            ev_b.append(("site", idx, (q,)))
+            q = IR.site_qubits(circuit.noises[idx][1])
+            ev_a.append(("site", idx, q))
+            ev_b.append(("site", idx, q))
     fa = [list(f[1]) for f in factors]
     fb = [list(f[2]) for f in factors]
     return Network(circuit.n, ev_a, fa), Network(circuit.n, ev_b, fb)

@@ -91,6 +91,54 @@ def near_identity_channel(rng, eps: float, n_kraus: int = 2) -> list:
     return [np.sqrt(1.0 - eps) * _I] + [np.sqrt(eps) * e for e in rest]
 
 
+def depolarizing2(p: float) -> list:
+    """Two-qubit depolarizing: rho -> (1-p) rho + p/15 sum_{P != II} P rho P,
+    P over the two-qubit Paulis; 4x4 Kraus operators indexed 2*b(q0) + b(q1)."""
+    if not 0.0 <= p <= 1.0:
+        raise ValueError("p must lie in [0, 1]")
+    paulis = [_I, _X, _Y, _Z]
+    out = [np.sqrt(1.0 - p) * np.kron(_I, _I)]
+    for a in range(4):
+        for b in range(4):
+            if a or b:
+                out.append(np.sqrt(p / 15.0) * np.kron(paulis[a], paulis[b]))
+    return out
+
+
+def random_channel2(rng, n_kraus: int) -> list:
+    """Seeded random two-qubit CPTP channel: blocks of a random 4k x 4 isometry."""
+    g = np.empty((4 * n_kraus, 4), dtype=np.complex128)
+    for i in range(4 * n_kraus):
+        for j in range(4):
+            g[i, j] = _gauss(rng) + 1j * _gauss(rng)
+    q, r = np.linalg.qr(g)
+    d = np.diag(r)
+    q = q * (d / np.abs(d))[None, :]
+    return [q[4 * k:4 * k + 4, :].copy() for k in range(n_kraus)]
+
+
+def near_identity_channel2(rng, eps: float, n_kraus: int = 2) -> list:
+    """(1-eps) two-qubit identity channel mixed with eps of a random one."""
+    rest = random_channel2(rng, n_kraus)
+    return [np.sqrt(1.0 - eps) * np.eye(4, dtype=np.complex128)] + [np.sqrt(eps) * e for e in rest]
+
+
+def matrix_of(kraus: list) -> np.ndarray:
+    """M = sum_k E_k (x) E_k^* (the input form of a noise given as a superoperator)."""
+    return sum(np.kron(e, e.conj()) for e in kraus)
+
+
+def perturbed_superop(rng, kraus: list, eps: float) -> np.ndarray:
+    """The matrix of a channel plus eps times a seeded random complex matrix:
+    a linear map on density matrices that is in general neither completely
+    positive nor Hermiticity preserving (its tensor-permuted matrix is not
+    positive semidefinite, so the two factor sets of the SVD differ)."""
+    m = matrix_of(kraus)
+    d = m.shape[0]
+    r = np.array([[_gauss(rng) + 1j * _gauss(rng) for _ in range(d)] for _ in range(d)])
+    return m + eps * r
+
+
 def _gauss(rng) -> float:
     # Box-Muller from two uniforms of the seeded generator
     u1 = max(rng.uniform(), 1e-300)

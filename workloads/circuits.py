@@ -32,8 +32,10 @@ GATE_NPARAM = {"h": 0, "x": 0, "y": 0, "z": 0, "t": 0, "rx": 1, "ry": 1, "rz": 1
 class Noise:
     after_gate: int          # index of the gate this noise follows (-1: before all gates)
     qubit: int
-    kraus: list              # list of 2x2 complex128 arrays
+    kraus: list              # list of 2x2 (4x4 for two qubits) complex128 arrays
     label: str = ""
+    qubit2: int = -1         # second qubit of a two-qubit noise (-1: one qubit)
+    superop: object = None   # instead of Kraus operators: the matrix representation M (4x4 or 16x16)
 
 
 @dataclass
