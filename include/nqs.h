@@ -160,6 +160,22 @@ int nqs_enumerate_terms(nqs_handle h, int level, uint64_t* rec, size_t cap, size
  * K[8*i + 2*(2a+b) + {0,1}] = K_i[a][b] (complex128), K_i = sqrt(d_i) A_i. */
 int nqs_noise_factors(nqs_handle h, uint32_t site, double* d4, double* K);
 
+/* Factors of site `site` of a circuit with general noises (two-qubit
+ * channels, records noise2; noises given by their matrix representation,
+ * records superop / superop2): the SVD M~ = S D T^dagger of the
+ * tensor-permuted matrix (Sec. IV, Fig. 3 in its general form).  *m receives
+ * the factor count d^2 (4 or 16 for one or two qubits), *dim the factor size
+ * d; when the arrays are not NULL: sv[m] the singular values (descending),
+ * KA and KB m x d x d complex128 (row-major, interleaved re/im) with
+ * KA_i = sqrt(d_i) reshape(S|i>), KB_i = sqrt(d_i) reshape(T|i>); a term is
+ * <v|C[KA_sigma]|psi> conj(<v|C[KB_sigma]|psi>), and KA = KB for channels.
+ * *same = 1 when KA = KB at this site.  Test hook.
+ * Errors: NQS_ERR_ARG (site out of range), NQS_ERR_ORDER (not prepared),
+ * NQS_ERR_UNSUPPORTED (the circuit has only one-qubit channels: see
+ * nqs_noise_factors). */
+int nqs_general_factors(nqs_handle h, uint32_t site, int32_t* m, int32_t* dim, int32_t* same, double* sv, double* KA,
+                        double* KB);
+
 /* Term values X of the last nqs_fidelity on this handle, in canonical order,
  * copied to host memory `out` (synchronises the stream of that call). */
 int nqs_term_values(nqs_handle h, double* out, size_t cap, size_t* count);

@@ -97,6 +97,27 @@ int nqs_prepare_noise(nqs_handle hh, const nqs_noise* sites, size_t n_sites, uin
     } else {
         ns = h->circ.noises;
     }
+    bool general = false;
+    for (const auto& s : ns) general = general || s.general();
+    if (general) {
+        // two-qubit or superoperator noises: every site goes through the general path
+        std::vector<GFactors> gf(ns.size());
+        for (size_t i = 0; i < ns.size(); ++i) {
+            int rc = factor_general(ns[i], gf[i]);
+            if (rc != NQS_OK) return rc;
+        }
+        engine_batch_forget(h);
+        engine_destroy(*h);
+        sets_destroy(*h);
+        general_destroy(*h);
+        h->circ.noises = ns;
+        h->factors.clear();
+        h->gfac = gf;
+        h->general = true;
+        h->plan = Plan{};
+        h->prepared = true;
+        return NQS_OK;
+    }
     std::vector<Factors> fac(ns.size());
     for (size_t i = 0; i < ns.size(); ++i) {
         int rc = factor_noise(ns[i], (flags & NQS_PREP_PRUNE_ZERO_RANK) != 0, fac[i]);
@@ -105,6 +126,9 @@ int nqs_prepare_noise(nqs_handle hh, const nqs_noise* sites, size_t n_sites, uin
     engine_batch_forget(h);
     engine_destroy(*h);
     sets_destroy(*h);
+    general_destroy(*h);
+    h->general = false;
+    h->gfac.clear();
     h->circ.noises = ns;
     h->factors = fac;
     build_plan(h->circ, h->factors, kTileQubits, h->plan);
@@ -135,6 +159,11 @@ int nqs_fidelity(nqs_handle hh, const nqs_state* psi, const nqs_state* v, int le
     if (rc) return rc;
     rc = check_state(*h, v, true);
     if (rc) return rc;
+    if (h->general) {
+        const int lvl = std::min(level, (int)h->gfac.size());
+        if (lvl > NQS_MAX_LEVEL) return NQS_ERR_ARG;
+        return general_fidelity(*h, psi, v, lvl, out, stream);
+    }
     int lvl = std::min(level, (int)h->factors.size());
     if (lvl > NQS_MAX_LEVEL) return NQS_ERR_ARG;
     return engine_fidelity(*h, psi, v, lvl, out, stream);
@@ -149,6 +178,7 @@ int nqs_batch_fidelity(const nqs_handle* hs, size_t count, const nqs_state* psis
         Handle* h = reinterpret_cast<Handle*>(hs[i]);
         if (!h || levels[i] < 0) return NQS_ERR_ARG;
         if (!h->prepared) return NQS_ERR_ORDER;
+        if (h->general) return NQS_ERR_UNSUPPORTED;   // one-qubit channels only
         int rc = check_state(*h, &psis[i], false);
         if (rc) return rc;
         rc = check_state(*h, &vs[i], true);
@@ -163,6 +193,7 @@ int nqs_batch_fidelity(const nqs_handle* hs, size_t count, const nqs_state* psis
 
 int nqs_enumerate_terms(nqs_handle hh, int level, uint64_t* rec, size_t cap, size_t* count) {
     Handle* h = reinterpret_cast<Handle*>(hh);
+    if (h && h->general) return NQS_ERR_UNSUPPORTED;   // one-qubit channels only
     if (!h || !count || level < 0 || (cap && !rec)) return NQS_ERR_ARG;
     if (!h->prepared) return NQS_ERR_ORDER;
     const int N = (int)h->factors.size();
@@ -208,6 +239,7 @@ int nqs_enumerate_terms(nqs_handle hh, int level, uint64_t* rec, size_t cap, siz
 
 int nqs_noise_factors(nqs_handle hh, uint32_t site, double* d4, double* K) {
     Handle* h = reinterpret_cast<Handle*>(hh);
+    if (h && h->general) return NQS_ERR_UNSUPPORTED;   // one-qubit channels only
     if (!h || !d4 || !K) return NQS_ERR_ARG;
     if (!h->prepared) return NQS_ERR_ORDER;
     if (site >= h->factors.size()) return NQS_ERR_ARG;
@@ -222,9 +254,36 @@ int nqs_noise_factors(nqs_handle hh, uint32_t site, double* d4, double* K) {
     return NQS_OK;
 }
 
+int nqs_general_factors(nqs_handle hh, uint32_t site, int32_t* m, int32_t* dim, int32_t* same, double* sv, double* KA,
+                        double* KB) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !m || !dim || !same) return NQS_ERR_ARG;
+    if (!h->prepared) return NQS_ERR_ORDER;
+    if (!h->general) return NQS_ERR_UNSUPPORTED;
+    if (site >= h->gfac.size()) return NQS_ERR_ARG;
+    const GFactors& f = h->gfac[site];
+    *m = f.m;
+    *dim = f.nq == 1 ? 2 : 4;
+    *same = f.same ? 1 : 0;
+    if (sv)
+        for (int i = 0; i < f.m; ++i) sv[i] = f.d[i];
+    for (size_t e = 0; e < f.KA.size(); ++e) {
+        if (KA) {
+            KA[2 * e] = f.KA[e].real();
+            KA[2 * e + 1] = f.KA[e].imag();
+        }
+        if (KB) {
+            KB[2 * e] = f.KB[e].real();
+            KB[2 * e + 1] = f.KB[e].imag();
+        }
+    }
+    return NQS_OK;
+}
+
 int nqs_term_values(nqs_handle hh, double* out, size_t cap, size_t* count) {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h || !count || (cap && !out)) return NQS_ERR_ARG;
+    if (h->general) return general_term_values(*h, out, cap, count);
     return engine_term_values(*h, out, cap, count);
 }
 
@@ -233,11 +292,14 @@ int nqs_truncation_bound(nqs_handle hh, int level, double* out) {
     if (!h || !out || level < 0) return NQS_ERR_ARG;
     if (!h->prepared) return NQS_ERR_ORDER;
     std::vector<double> poly(1, 1.0);
-    for (const auto& f : h->factors) {
+    std::vector<std::pair<double, double>> norms;
+    for (const auto& f : h->factors) norms.push_back({f.norm_dom, f.norm_rest});
+    for (const auto& f : h->gfac) norms.push_back({f.norm_dom, f.norm_rest});
+    for (const auto& nr : norms) {
         std::vector<double> nx(poly.size() + 1, 0.0);
         for (size_t i = 0; i < poly.size(); ++i) {
-            nx[i] += poly[i] * f.norm_dom;
-            nx[i + 1] += poly[i] * f.norm_rest;
+            nx[i] += poly[i] * nr.first;
+            nx[i + 1] += poly[i] * nr.second;
         }
         poly.swap(nx);
     }
@@ -253,7 +315,7 @@ int nqs_fidelity_adaptive(nqs_handle hh, const nqs_state* psi, const nqs_state* 
     if (!h || !out || !(tol >= 0.0) || max_level < 0) return NQS_ERR_ARG;
     if (!(criteria & (NQS_ADAPT_BOUND | NQS_ADAPT_OBSERVED)) || (criteria & ~3u)) return NQS_ERR_ARG;
     if (!h->prepared) return NQS_ERR_ORDER;
-    const int N = (int)h->factors.size();
+    const int N = (int)(h->general ? h->gfac.size() : h->factors.size());
     int top = std::min(std::min(max_level, N), NQS_MAX_LEVEL);
     if (criteria & NQS_ADAPT_BOUND) {
         // smallest level whose truncation bound is within tol
@@ -285,7 +347,7 @@ int nqs_offdiagonal(nqs_handle hh, const nqs_state* psi, const nqs_state* x, con
     int rc = check_state(*h, psi, false);
     if (rc) return rc;
     if (check_state(*h, x, false) || check_state(*h, y, false)) return NQS_ERR_ARG;
-    const int lvl = std::min(level, (int)h->factors.size());
+    const int lvl = std::min(level, (int)(h->general ? h->gfac.size() : h->factors.size()));
     if (lvl > NQS_MAX_LEVEL) return NQS_ERR_ARG;
     const long long dim = 1ll << h->circ.n;
     const size_t bytes = (size_t)dim * 8;
@@ -310,7 +372,7 @@ int nqs_offdiagonal(nqs_handle hh, const nqs_state* psi, const nqs_state* x, con
         vs.kind = NQS_STATE_DENSE;
         vs.dev = v;
         nqs_result r{};
-        rc = engine_fidelity(*h, psi, &vs, lvl, &r, stream);
+        rc = h->general ? general_fidelity(*h, psi, &vs, lvl, &r, stream) : engine_fidelity(*h, psi, &vs, lvl, &r, stream);
         if (rc == NQS_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = NQS_ERR_CUDA;
         if (rc != NQS_OK) break;
         if (parts) parts[k] = r;
@@ -420,6 +482,7 @@ int nqs_get_option(nqs_handle hh, int option, int64_t* value) {
 int nqs_autotune(nqs_handle hh, const nqs_state* psi, const nqs_state* v, int level, int trials, nqs_result* out,
                  void* stream) {
     Handle* h = reinterpret_cast<Handle*>(hh);
+    if (h && h->general) return NQS_ERR_UNSUPPORTED;   // one-qubit channels only
     if (!h || trials < 1 || level < 0) return NQS_ERR_ARG;
     if (!h->prepared) return NQS_ERR_ORDER;
     cudaStream_t st = (cudaStream_t)stream;
@@ -507,6 +570,7 @@ size_t nqs_reduced_matrix_scratch_bytes(int n) {
 
 int nqs_prepare_sets(nqs_handle hh, const nqs_state* psi, const nqs_state* v, void* stream) {
     Handle* h = reinterpret_cast<Handle*>(hh);
+    if (h && h->general) return NQS_ERR_UNSUPPORTED;   // one-qubit channels only
     if (!h) return NQS_ERR_ARG;
     if (!h->prepared) return NQS_ERR_ORDER;
     int rc = check_state(*h, psi, false);
@@ -518,6 +582,7 @@ int nqs_prepare_sets(nqs_handle hh, const nqs_state* psi, const nqs_state* v, vo
 
 int nqs_eval_sets(nqs_handle hh, int k, const int32_t* sets, size_t m, double* W_out, void* stream) {
     Handle* h = reinterpret_cast<Handle*>(hh);
+    if (h && h->general) return NQS_ERR_UNSUPPORTED;   // one-qubit channels only
     if (!h || !sets || !W_out || k < 1 || k > 3) return NQS_ERR_ARG;
     if (m == 0) return NQS_OK;
     return engine_eval_sets(*h, k, sets, m, W_out, stream);
@@ -564,6 +629,7 @@ void nqs_mlp_destroy(nqs_mlp m) { mlp_destroy(reinterpret_cast<Mlp*>(m)); }
 
 int nqs_site_features(nqs_handle hh, const double* W1, float* out) {
     Handle* h = reinterpret_cast<Handle*>(hh);
+    if (h && h->general) return NQS_ERR_UNSUPPORTED;   // one-qubit channels only
     if (!h || !W1 || !out) return NQS_ERR_ARG;
     if (!h->prepared) return NQS_ERR_ORDER;
     return site_features(*h, W1, out);
@@ -572,6 +638,7 @@ int nqs_site_features(nqs_handle hh, const double* W1, float* out) {
 int nqs_pair_training_data(nqs_handle hh, const float* feats, const double* W2, float* X, float* y, size_t cap,
                            size_t* count) {
     Handle* h = reinterpret_cast<Handle*>(hh);
+    if (h && h->general) return NQS_ERR_UNSUPPORTED;   // one-qubit channels only
     if (!h || !feats || !W2 || !count || (cap && (!X || !y))) return NQS_ERR_ARG;
     if (!h->prepared) return NQS_ERR_ORDER;
     return pair_training_data(*h, feats, W2, X, y, cap, count);
@@ -580,6 +647,7 @@ int nqs_pair_training_data(nqs_handle hh, const float* feats, const double* W2, 
 int nqs_is_estimate(nqs_handle hh, nqs_mlp mlp, int level, uint64_t samples, double alpha, uint64_t seed,
                     const float* feats, const double* W1, nqs_is_result* out, void* stream) {
     Handle* h = reinterpret_cast<Handle*>(hh);
+    if (h && h->general) return NQS_ERR_UNSUPPORTED;   // one-qubit channels only
     if (!h || !out || (mlp && (!feats || !W1)) || (!W1)) return NQS_ERR_ARG;
     if (!h->prepared) return NQS_ERR_ORDER;
     return is_estimate(*h, reinterpret_cast<Mlp*>(mlp), level, samples, alpha, seed, feats, W1, out, stream);
@@ -588,6 +656,7 @@ int nqs_is_estimate(nqs_handle hh, nqs_mlp mlp, int level, uint64_t samples, dou
 int nqs_is_proposal(nqs_handle hh, nqs_mlp mlp, int level, double alpha, const float* feats, const double* W1,
                     double* q_out, size_t cap, size_t* count, void* stream) {
     Handle* h = reinterpret_cast<Handle*>(hh);
+    if (h && h->general) return NQS_ERR_UNSUPPORTED;   // one-qubit channels only
     if (!h || !count || !W1 || (mlp && !feats)) return NQS_ERR_ARG;
     if (!h->prepared) return NQS_ERR_ORDER;
     return is_proposal_values(*h, reinterpret_cast<Mlp*>(mlp), level, alpha, feats, W1, q_out, cap, count, stream);
@@ -599,6 +668,7 @@ void nqs_destroy(nqs_handle hh) {
     engine_batch_forget(h);
     engine_destroy(*h);
     sets_destroy(*h);
+    general_destroy(*h);
     delete h;
 }
 

@@ -117,6 +117,40 @@ int parse_circuit(const char* text, Circuit& out, std::string& err) {
                 s.kraus.push_back(m);
             }
             out.noises.push_back(s);
+        } else if (tok[0] == "noise2" || tok[0] == "superop" || tok[0] == "superop2") {
+            // general noises: two-qubit Kraus operators (4x4, index 2*b(q0) + b(q1)),
+            // or the matrix representation M of a one- / two-qubit noise
+            if (!header || out.n == 0) return fail("noise before header/qubits");
+            const bool two = tok[0] != "superop";
+            const bool sop = tok[0] != "noise2";
+            long long ag, q, q2 = -1, k = 1;
+            size_t at = 2;
+            if (tok.size() < 3 || !parse_int(tok[1], ag) || !parse_int(tok[at++], q)) return fail("bad noise record");
+            if (two && (tok.size() <= at || !parse_int(tok[at++], q2))) return fail("bad noise record");
+            if (!sop && (tok.size() <= at || !parse_int(tok[at++], k))) return fail("bad noise record");
+            if (q < 0 || q >= out.n || (two && (q2 < 0 || q2 >= out.n || q2 == q))) return fail("bad noise qubit");
+            if (k < 1 || k > 16) return fail("Kraus count outside 1..16");
+            const int d = two ? 4 : 2;
+            const size_t vals = sop ? (size_t)2 * d * d * d * d : (size_t)2 * d * d * k;
+            if (tok.size() != at + vals) return fail("wrong value count");
+            std::vector<cd> all(vals / 2);
+            for (size_t e = 0; e < all.size(); ++e) {
+                double re, im;
+                if (!parse_double(tok[at + 2 * e], re) || !parse_double(tok[at + 2 * e + 1], im))
+                    return fail("bad value");
+                all[e] = cd(re, im);
+            }
+            NoiseSite s;
+            s.after_gate = (int)ag;
+            s.qubit = (int)q;
+            s.qubit2 = two ? (int)q2 : -1;
+            if (sop) {
+                s.superop = all;
+            } else {
+                for (long long j = 0; j < k; ++j)
+                    s.kraus_d.emplace_back(all.begin() + j * d * d, all.begin() + (j + 1) * d * d);
+            }
+            out.noises.push_back(s);
         } else {
             return fail("unknown record " + tok[0]);
         }

@@ -31,6 +31,13 @@ struct NoiseSite {
     int after_gate = -1;               // -1: before gate 0
     int qubit = 0;
     std::vector<Mat2> kraus;
+    // general noises (IR records noise2 / superop / superop2): a second qubit,
+    // d x d Kraus operators (d = 4), or the matrix representation M itself
+    int qubit2 = -1;
+    std::vector<std::vector<cd>> kraus_d;   // row-major d x d
+    std::vector<cd> superop;                // row-major d^2 x d^2
+    bool general() const { return qubit2 >= 0 || !superop.empty(); }
+    int dim() const { return qubit2 >= 0 ? 4 : 2; }
 };
 
 struct Circuit {
@@ -106,8 +113,29 @@ void build_plan(const Circuit& c, const std::vector<Factors>& f, int tile_qubits
 std::vector<PassSpec> segment(const Plan& p, bool cut_after_sites, int max_sites_per_pass, int max_ops_per_pass,
                               const std::vector<char>* cut_after = nullptr);
 
+// ------------------------------------------ general noises (generic.cu)
+// Factors of a one- or two-qubit noise given by Kraus operators or by its
+// matrix representation: M~ = S D T^dagger (one-sided Jacobi SVD, FP64),
+// KA_i = sqrt(d_i) reshape(S|i>), KB_i = sqrt(d_i) reshape(T|i>); a term is
+// X = <v|C[KA_sigma]|psi> conj(<v|C[KB_sigma]|psi>).  For a channel M~ is PSD
+// and KA = KB.
+struct GFactors {
+    int nq = 1, q0 = 0, q1 = -1;       // site qubits
+    int m = 4;                         // factors (d^2), index 0 dominant
+    std::vector<double> d;             // singular values, descending
+    std::vector<cd> KA, KB;            // m x (dim x dim), row-major
+    bool same = true;                  // KA == KB (one network per term)
+    double norm_dom = 0, norm_rest = 0;
+};
+int factor_general(const NoiseSite& s, GFactors& out);
+// complex one-sided Jacobi SVD of a square n x n matrix (row-major):
+// a = U diag(sv) V^dagger, singular values descending; U, V column-major
+// as u[col * n + row]
+void svd_jacobi(const std::vector<cd>& a, int n, std::vector<double>& sv, std::vector<cd>& u, std::vector<cd>& v);
+
 // ------------------------------------------------------------------- handle
 struct Engine;     // device-side state (engine.cu)
+struct GEngine;    // general-noise path state (generic.cu)
 struct SetsState;  // checkpoints for site-set evaluation (sets.cu)
 
 struct Handle {
@@ -125,7 +153,15 @@ struct Handle {
     int opt_max_ops = 0;           // operations per pass (segmentation)
     int opt_max_sites = 0;         // sites per pass (segmentation)
     int opt_jit = 0;               // pass-specialised kernels: 0 auto, 1 always, 2 never
+    // general noises: the circuit is evaluated by the general-noise path
+    bool general = false;
+    std::vector<GFactors> gfac;
+    GEngine* geng = nullptr;
 };
+int general_fidelity(Handle& h, const nqs_state* psi, const nqs_state* v, int level, nqs_result* out,
+                     void* stream);
+int general_term_values(Handle& h, double* out, size_t cap, size_t* count);
+void general_destroy(Handle& h);
 
 // engine entry points (engine.cu)
 int engine_fidelity(Handle& h, const nqs_state* psi, const nqs_state* v, int level,

@@ -116,6 +116,9 @@ _SIGS = {
     "nqs_term_values": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t,
                                        ctypes.POINTER(ctypes.c_size_t)]),
     "nqs_truncation_bound": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "nqs_general_factors": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "nqs_offdiagonal": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(nqs_state), ctypes.POINTER(nqs_state),
                                        ctypes.POINTER(nqs_state), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(nqs_result), ctypes.c_void_p]),
@@ -375,6 +378,22 @@ def nqs_offdiagonal(h, psi, x, y, level, stream=None):
     _check(_lib().nqs_offdiagonal(h, ctypes.byref(ps), ctypes.byref(xs), ctypes.byref(ys), int(level), out, parts,
                                   _stream_ptr(stream)), "nqs_offdiagonal")
     return complex(out[0], out[1]), [parts[k].to_dict() for k in range(4)]
+
+
+def nqs_general_factors(h, site):
+    """(singular values, KA, KB, same) of a general-noise site as numpy arrays
+    (KA, KB: m x d x d complex128)."""
+    import numpy as np
+    m, d, same = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib().nqs_general_factors(h, site, ctypes.byref(m), ctypes.byref(d), ctypes.byref(same), None, None, None),
+           "nqs_general_factors")
+    sv = np.zeros(m.value)
+    ka = np.zeros((m.value, d.value, d.value), np.complex128)
+    kb = np.zeros_like(ka)
+    _check(_lib().nqs_general_factors(h, site, ctypes.byref(m), ctypes.byref(d), ctypes.byref(same),
+                                      sv.ctypes.data_as(ctypes.c_void_p), ka.ctypes.data_as(ctypes.c_void_p),
+                                      kb.ctypes.data_as(ctypes.c_void_p)), "nqs_general_factors")
+    return sv, ka, kb, bool(same.value)
 
 
 def nqs_get_info(h):

@@ -178,3 +178,41 @@ def test_prune_flag_drops_zero_rank_factors():
             if site < 2:
                 assert fac == 1
     nqs.nqs_destroy(h)
+
+
+# ----------------------------------------------------------------------------
+# general noises (two-qubit channels, superoperators): host factors
+
+def _general_workload(seed):
+    from workloads.circuits import Noise
+    rng = W.SplitMix64(seed)
+    w = W.random_circuit(seed, 4, 20, 0, v_kind="ideal")
+    w.noises = [Noise(2, 1, ch.near_identity_channel2(rng, 0.03, 2), "", 3),
+                Noise(5, 0, [], "", -1, ch.perturbed_superop(rng, ch.amplitude_damping(0.05), 0.01)),
+                Noise(9, 2, ch.depolarizing_paper(0.02), ""),
+                Noise(12, 3, [], "", 0, ch.perturbed_superop(rng, ch.depolarizing2(0.04), 0.005)),
+                Noise(15, 0, ch.depolarizing2(0.05), "", 2)]
+    return w
+
+
+def test_general_factors_rebuild_the_noise_matrix():
+    import numpy as np
+    from oracle import expansion as OEX
+    from oracle import ir as OIR
+    w = _general_workload(7)
+    c = OIR.parse(W.to_ir_text(w))
+    h = nqs.nqs_load_circuit(W.to_ir_text(w))
+    nqs.nqs_prepare_noise(h)
+    for s, (_, q, spec) in enumerate(c.noises):
+        sv, ka, kb, same = nqs.nqs_general_factors(h, s)
+        m = OEX.matrix_representation(spec)
+        d_ref = OEX.svd_factors(spec)[0]
+        assert np.allclose(sv, d_ref, rtol=1e-10, atol=1e-13)
+        # sum_i KA_i (x) conj(KB_i) = M (the factors carry the whole noise)
+        rebuilt = sum(np.kron(a, b.conj()) for a, b in zip(ka, kb))
+        assert np.allclose(rebuilt, m, atol=1e-12)
+        assert same == (not isinstance(spec, OIR.SuperOp))
+    with pytest.raises(nqs.NqsError) as e:
+        nqs.nqs_noise_factors(h, 0)
+    assert e.value.code == nqs.NQS_ERR_UNSUPPORTED
+    nqs.nqs_destroy(h)
