@@ -581,13 +581,23 @@ done:
 typedef struct {
     int64_t max, done;
     int dry, stop;
+    int64_t untimed;       /* passes run before the clock starts */
+    int started;
+    double t0, excluded, excl0;
 } Budget;
+
+static double now_s(void);
 
 static int take(Budget* b) {
     if (b->stop) return 0;
     if (b->done >= b->max) {
         b->stop = 1;
         return 0;
+    }
+    if (!b->started && b->done >= b->untimed) {
+        b->started = 1;
+        b->t0 = now_s();
+        b->excl0 = b->excluded;
     }
     b->done++;
     return !b->dry;
@@ -602,11 +612,11 @@ static double now_s(void) {
 /* A state for the timed call, its pages touched at once (zeroed) and the time
  * that takes added to *excluded: the first touch of fresh memory is paid once
  * per state of a complete call, which a short sample would overweight. */
-static cplx* new_state_touched(int n, double* excluded) {
+static cplx* new_state_touched(int n, double* excluded_) {
     const double t0 = now_s();
     cplx* p = new_state(n);
     if (p) memset(p, 0, ((size_t)1 << n) * sizeof(cplx));
-    *excluded += now_s() - t0;
+    *excluded_ += now_s() - t0;
     return p;
 }
 
@@ -644,15 +654,16 @@ static void expand_budget(const O3* o, cplx* w, int e0, int depth, Bufs* B, Budg
  * (v_bits < 0), backward checkpoints, then
  * the depth-first forward sweep -- executed pass by pass until `max_passes`
  * passes are done (amplitudes are not kept), or, with dry = 1, only counted.
- * Returns the passes executed (or counted) and, in *seconds, their time (the
- * allocation and first touch of each state excluded); the caller scales by
- * the pass count of the complete call.  Returns -1 when a state cannot be
- * allocated.
+ * Returns the passes executed (or counted) and, in *seconds, the time of the
+ * passes after the first `untimed` ones (the single-threaded set-up of the
+ * input states), allocation and first touch of each state excluded; the
+ * caller scales by the pass count of the complete call.  Returns -1 when a
+ * state cannot be allocated.
  */
 int64_t nqso3_timed_passes(int n, int n_ev, const int* kind, const int* nq, const int* q0, const int* q1,
                            const int* site, const double* mat, int n_sites, const int* m, const double* fac,
                            int64_t psi_bits, int64_t v_bits, const double* bra, int level, int64_t max_passes,
-                           int dry, double* seconds, int threads) {
+                           int64_t untimed, int dry, double* seconds, int threads) {
 #ifdef _OPENMP
     if (threads > 0) omp_set_num_threads(threads);
 #else
@@ -667,13 +678,15 @@ int64_t nqso3_timed_passes(int n, int n_ev, const int* kind, const int* nq, cons
     const int64_t dim = (int64_t)1 << n;
     for (int e = 0; e < n_ev; ++e)
         if (kind[e] == 1) o.last_site_ev = e;
-    Budget bu = {max_passes, 0, dry, 0};
+    Budget bu;
+    memset(&bu, 0, sizeof bu);
+    bu.max = max_passes;
+    bu.dry = dry;
+    bu.untimed = untimed;
     int64_t rc = 0;
-    double excluded = 0.0;
-    const double t_start = now_s();
-    cplx* psi = dry ? NULL : new_state_touched(n, &excluded);
-    cplx* v = dry ? NULL : new_state_touched(n, &excluded);
-    cplx* p = dry ? NULL : new_state_touched(n, &excluded);
+    cplx* psi = dry ? NULL : new_state_touched(n, &bu.excluded);
+    cplx* v = dry ? NULL : new_state_touched(n, &bu.excluded);
+    cplx* p = dry ? NULL : new_state_touched(n, &bu.excluded);
     Bufs B;
     B.work = (cplx**)calloc((size_t)level + 1, sizeof(cplx*));
     o.phi = (cplx**)calloc((size_t)n_sites, sizeof(cplx*));
@@ -701,7 +714,7 @@ int64_t nqso3_timed_passes(int n, int n_ev, const int* kind, const int* nq, cons
         } else {
             const int t = site[e];
             if (!dry && !bu.stop) {
-                o.phi[t] = new_state_touched(n, &excluded);
+                o.phi[t] = new_state_touched(n, &bu.excluded);
                 if (!o.phi[t]) { rc = -1; goto done; }
             }
             if (take(&bu)) memcpy(o.phi[t], p, (size_t)dim * sizeof(cplx));
@@ -710,13 +723,13 @@ int64_t nqso3_timed_passes(int n, int n_ev, const int* kind, const int* nq, cons
     }
     if (!dry && !bu.stop)
         for (int dd = 0; dd <= level; ++dd) {
-            B.work[dd] = new_state_touched(n, &excluded);
+            B.work[dd] = new_state_touched(n, &bu.excluded);
             if (!B.work[dd]) { rc = -1; goto done; }
         }
     if (take(&bu)) memcpy(B.work[0], psi, (size_t)dim * sizeof(cplx));
     expand_budget(&o, B.work[0], 0, 0, &B, &bu);
     rc = bu.done;
-    if (seconds) *seconds = now_s() - t_start - excluded;
+    if (seconds) *seconds = bu.started ? now_s() - bu.t0 - (bu.excluded - bu.excl0) : 0.0;
 done:
     free(psi);
     free(v);

@@ -57,7 +57,7 @@ def lib():
         L.nqso3_set_amplitudes.restype = ctypes.c_int
         L.nqso3_timed_passes.argtypes = [ctypes.c_int, ctypes.c_int, ip, ip, ip, ip, ip, dp, ctypes.c_int, ip, dp,
                                          ctypes.c_int64, ctypes.c_int64, dp, ctypes.c_int, ctypes.c_int64,
-                                         ctypes.c_int, P(ctypes.c_double), ctypes.c_int]
+                                         ctypes.c_int64, ctypes.c_int, P(ctypes.c_double), ctypes.c_int]
         L.nqso3_timed_passes.restype = ctypes.c_int64
         L.nqso3_term_count.argtypes = [ctypes.c_int, ip, ctypes.c_int]
         L.nqso3_term_count.restype = ctypes.c_int64
@@ -153,7 +153,7 @@ class Network:
         return res
 
 
-    def passes(self, psi_bits, v_bits, bra, level, max_passes, dry, threads=0):
+    def passes(self, psi_bits, v_bits, bra, level, max_passes, dry, threads=0, untimed=0):
         """State passes of this network's wide-state call (see
         nqso3_timed_passes): executed up to max_passes, or only counted.
         bra=None: the bra is |v_bits>, or v = U|psi_bits> when v_bits < 0."""
@@ -167,8 +167,8 @@ class Network:
         secs = ctypes.c_double(0.0)
         r = lib().nqso3_timed_passes(self.n, len(self.kind), _ip(self.kind), _ip(self.nq), _ip(self.q0),
                                      _ip(self.q1), _ip(self.site), _dp(mat), len(self.m), _ip(self.m), _dp(fac),
-                                     int(psi_bits), int(v_bits), bp, level, int(max_passes), 1 if dry else 0,
-                                     ctypes.byref(secs), threads)
+                                     int(psi_bits), int(v_bits), bp, level, int(max_passes), int(untimed),
+                                     1 if dry else 0, ctypes.byref(secs), threads)
         if r < 0:
             raise MemoryError("O3: a state does not fit in host memory")
         self.last_seconds = secs.value
@@ -249,12 +249,13 @@ def set_weights(circuit, psi_spec, v_spec, sets, threads=0, factors=None):
     return np.array([complex(np.sum(x * y)) for x, y in zip(a, b)])
 
 
-def timed_sample(circuit, psi_bits, v_bits, level, max_passes, threads=0):
+def timed_sample(circuit, psi_bits, v_bits, level, max_passes, threads=0, untimed=2):
     """Time the first `max_passes` state passes of O3's complete call
     (psi = |psi_bits>, v = |v_bits> or, for v_bits < 0, U|psi> computed in C;
     both networks), and count
     the passes of the complete call.  Returns (passes_done, passes_total,
-    seconds of those passes, allocation and first touch of states excluded):
+    seconds of the passes after the first `untimed` -- the set-up of psi and
+    v -- allocation and first touch of states excluded):
     the call's time is seconds * passes_total / passes_done when every pass
     sweeps the full state, as here."""
     na, nb = networks(circuit)
@@ -262,5 +263,5 @@ def timed_sample(circuit, psi_bits, v_bits, level, max_passes, threads=0):
     dummy = np.zeros(1, np.complex128)
     total = (na.passes(psi_bits, v_bits, None, level, 1 << 62, True) +
              nb.passes(psi_bits, v_bits, dummy, level, 1 << 62, True) + 1)
-    done = na.passes(psi_bits, v_bits, None, level, max_passes, False, threads)
-    return done, total, na.last_seconds
+    done = na.passes(psi_bits, v_bits, None, level, max_passes, False, threads, untimed)
+    return max(done - untimed, 0), total, na.last_seconds

@@ -156,5 +156,5 @@ def test_o3_timed_sample_predicts_the_complete_call():
     pred = secs * total / done
     assert 0.4 * full < pred < 2.5 * full, (pred, full)
     # and the pass count is that of the call: counting twice gives the same
-    d2, t2, _ = O3.timed_sample(c, 0, -1, 2, 1)
+    d2, t2, _ = O3.timed_sample(c, 0, -1, 2, 3, untimed=2)
     assert t2 == total and d2 == 1

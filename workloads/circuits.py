@@ -250,10 +250,11 @@ def c4_batch(count: int = 512) -> list:
 
 
 def c5_grid(seed: int = 5, cols: int = 7, rows: int = 4, depth: int = 24,
-            n_noise: int = 200) -> Workload:
+            n_noise: int = 200, rate_lo: float = 1e-4, rate_hi: float = 5e-3) -> Workload:
     """4 x cols grid random circuit with n_noise mixed noises placed after the
     U3 gate of (layer, qubit) slots whose column is < 5, so the 4x5 twin
-    (cols=5) with the same seed carries the identical noise layout."""
+    (cols=5) with the same seed carries the identical noise layout.  Rates are
+    log-uniform in [rate_lo, rate_hi] (the draws do not depend on the range)."""
     rng = SplitMix64(seed)
     n = rows * cols
     # angles for a 4x7 grid are drawn for every (layer, row, col<7) so that the
@@ -269,7 +270,7 @@ def c5_grid(seed: int = 5, cols: int = 7, rows: int = 4, depth: int = 24,
     chosen = sorted(rng.choice_distinct(len(slots), n_noise))
     noise_spec = {}
     for k in chosen:
-        kraus, label = mixed_noise_kraus(rng, 1e-4, 5e-3)
+        kraus, label = mixed_noise_kraus(rng, rate_lo, rate_hi)
         noise_spec[slots[k]] = (kraus, label)
     gates, noises = [], []
     for layer in range(depth):
@@ -285,8 +286,16 @@ def c5_grid(seed: int = 5, cols: int = 7, rows: int = 4, depth: int = 24,
                     {"kind": "basis", "bits": 0}, {"kind": "ideal"}, (3,))
 
 
-def c5_twin(seed: int = 5) -> Workload:
-    return c5_grid(seed, cols=5)
+def c5_twin(seed: int = 5, rate_lo: float = 1e-4, rate_hi: float = 5e-3) -> Workload:
+    return c5_grid(seed, cols=5, rate_lo=rate_lo, rate_hi=rate_hi)
+
+
+def c5_twin_hot(seed: int = 5) -> Workload:
+    """The twin with rates from the upper part of the range, [1e-3, 5e-3]: its
+    level-3 sum exceeds 1e-6, so reaching |dF| <= 1e-6 needs level 3."""
+    w = c5_twin(seed, 1e-3, 5e-3)
+    w.name = "c5_twin_hot"
+    return w
 
 
 # ----------------------------------------------------------------------------
