@@ -51,6 +51,8 @@ WORKLOADS = {
     "qaoa24_l2": ("qaoa24", 2, "QAOA MaxCut n=24 (3-regular, p=4), 20 depolarizing, v=U|psi>, level 2"),
     "batch512": ("c4_batch", None, "512 circuits: width U{12..24}, depth U{10..30}, grid or line U3+CZ, "
                  "5-40 mixed AD/PD/depolarizing noises (rates 1e-4..1e-2), level U{1,2}, v=U|psi>"),
+    "c5_is28": ("c5_grid", 3, "4x7 grid depth 24, 200 mixed noises (rates 1e-4..5e-3), v=U|psi>: level 2 by "
+                "enumeration, level 3 by importance sampling with the learned proposal (n=28 states of 2 GiB)"),
     "twin20_is": ("c5_twin_hot", 3, "4x5 grid depth 24 (666 gates), 200 mixed noises (rates 1e-3..5e-3), v=U|psi>: "
                   "level 3 by importance sampling with the learned proposal, judged against full enumeration"),
 }
@@ -664,6 +666,75 @@ def run_twin_is(args):
     return 0
 
 
+def run_c5_is28(args):
+    """The 28-qubit, 200-noise grid circuit at full size: the level-2
+    expansion (179,701 terms; checkpoints spaced as memory requires), site
+    features and pair targets from its term values, the proposal network
+    trained on the GPU, site-set checkpoints, and T_3 by importance sampling
+    (2,000 draws).  The exact level-3 sum is out of reach at this width (35.6 M
+    terms); its estimator is judged on the n = 20 twin (twin20_is)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2211_17028_gb300 import nqs
+
+    torch.cuda.set_device(0)
+    nqs.use_torch_allocator()
+    w = W.c5_grid()
+    N = w.n_noise
+    circ = nqs.NoisyCircuit(W.to_ir_text(w))
+    psi, v = nqs.basis(w.psi["bits"]), nqs.ideal()
+
+    def timed(f):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = f()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    r2, t2 = timed(lambda: circ.fidelity(psi, v, 2))
+    info = nqs.nqs_get_info(circ.h)
+
+    def learn():
+        vals = circ.term_values()
+        W1 = vals[1:1 + 3 * N].reshape(-1, 3).sum(1)
+        W2f = vals[1 + 3 * N:].reshape(-1, 9).sum(1)
+        W2 = np.zeros((N, N))
+        iu = np.triu_indices(N, 1)
+        W2[iu] = W2f
+        W2 = W2 + W2.T
+        feats = nqs.nqs_site_features(circ.h, W1)
+        X, y = nqs.nqs_pair_training_data(circ.h, feats, W2)
+        m = nqs.nqs_mlp_create(8, 256, 3, seed=1)
+        nqs.nqs_mlp_train(m, torch.tensor(X, device="cuda"), torch.tensor(y, device="cuda"), batch=1024,
+                          steps=2000, lr=2e-3, seed=1)
+        return m, feats, W1
+    (m, feats, W1), t_train = timed(learn)
+    _, t_sets = timed(lambda: nqs.nqs_prepare_sets(circ.h, psi, v))
+    est, t_is = timed(lambda: nqs.nqs_is_estimate(circ.h, m, 3, 2000, 0.3, 99, feats, W1))
+    clk = clocks.stop()
+    nqs.nqs_mlp_destroy(m)
+    circ.close()
+    total = t2 + t_train + t_sets + t_is
+    line = {"metric": METRIC, "value": r2["n_terms"] / t2, "unit": "level-2 terms/s", "n_gpus": 1, "steps": 1,
+            "warmup": 0, "ms_per_step": 1000.0 * total, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64 sweeps, bf16/fp32 network", "data": "synthetic",
+            "config": {"workload": "c5_is28", "description": WORKLOADS["c5_is28"][2], "n_qubits": w.n,
+                       "gates": len(w.gates), "noises": N, "samples": 2000, "alpha": 0.3,
+                       "l2": "inputs larger than L2 (2 GiB states)"},
+            "level2": {"F": r2["F"], "T": r2["T"], "s": t2, "terms": r2["n_terms"], "bound": r2["bound"],
+                       "ckpt_spacing": info["ckpt_spacing"], "n_states": info["n_states"],
+                       "jit_launches": info["jit_launches"]},
+            "training_s": t_train, "site_set_checkpoints_s": t_sets,
+            "level3_is": {"T3": est["estimate"], "stderr": est["stderr_"], "ess": est["ess"],
+                          "distinct_sets": est["distinct"], "s": t_is, "status": est["status"]},
+            "F_level2_plus_T3": r2["F"] + est["estimate"], "total_s": total, "clocks": clk}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -672,6 +743,8 @@ def main():
         return run_batch(args)
     if args.workload == "twin20_is":
         return run_twin_is(args)
+    if args.workload == "c5_is28":
+        return run_c5_is28(args)
     return run_nqs(args)
 
 
