@@ -1,7 +1,8 @@
 // Proposal network of the importance-sampled level-l estimate: a small MLP
 // (ReLU hidden layers, linear scalar output) whose weights are used in bf16
 // with fp32 accumulation, trained on the GPU by the kernels below (forward,
-// backward, Adam on fp32 master weights, mean-squared-error loss).
+// backward, Adam on fp32 master weights, mean-squared-error loss).  The
+// matrix products run on the bf16 tensor cores (warp-level mma.sync).
 //
 // Parameters, flattened in this order: for each layer l, W_l (out x in,
 // row-major) then b_l (out).  The bf16 copy of every W_l is what the forward
@@ -10,7 +11,9 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "nqs_internal.h"
@@ -19,60 +22,124 @@ namespace nqs {
 
 namespace {
 
-constexpr int kTile = 32;
-
-// C[M x N] = op(A)[M x K] * op(B)[K x N] (+ bias[N]) (+ ReLU), fp32 accumulation.
+// C[M x N] = op(A)[M x K] * op(B)[K x N] (+ bias[N]) (+ ReLU), on the bf16
+// tensor cores (mma.sync m16n8k16, fp32 accumulation).
 //   A: fp32, row-major; transA -> A stored [K x M]
 //   B: bf16 (weights) or fp32, row-major; transB -> B stored [N x K]
 //   accumulate: C += result (weight gradients)
+// Both MMA operands are bf16, so an fp32 operand x enters as two bf16 parts,
+// x_hi = bf16(x) and x_lo = bf16(x - x_hi) (x = x_hi + x_lo to about 2^-16 of
+// |x|): C = A_hi B + A_lo B for bf16 weights, A_hi B_hi + A_lo B_hi + A_hi B_lo
+// when both are fp32 (the lo * lo product is below fp32 resolution).
+// Block tile 64 x 64, k-step 16, 4 warps of 32 x 32 (2 x 4 MMAs of 16 x 8).
+constexpr int kBM = 64, kBN = 64, kBK = 16, kPad = 8;
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
 template <typename TB, bool TA_T, bool TB_T>
-__global__ void gemm_kernel(int M, int N, int K, const float* __restrict__ A, const TB* __restrict__ B,
-                            float* __restrict__ C, const float* __restrict__ bias, int relu, int accumulate) {
-    __shared__ float As[kTile][kTile + 1];
-    __shared__ float Bs[kTile][kTile + 1];
-    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8 threads, each 4 rows
-    const int row0 = blockIdx.y * kTile, col = blockIdx.x * kTile + tx;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int k0 = 0; k0 < K; k0 += kTile) {
-        for (int r = ty; r < kTile; r += 8) {
-            const int m = row0 + r, k = k0 + tx;
+__global__ void __launch_bounds__(128) gemm_kernel(int M, int N, int K, const float* __restrict__ A,
+                                                   const TB* __restrict__ B, float* __restrict__ C,
+                                                   const float* __restrict__ bias, int relu, int accumulate) {
+    constexpr bool kSplitB = !std::is_same<TB, __nv_bfloat16>::value;
+    // tiles: A as [m][k], B as [n][k] (k contiguous: one 32-bit word holds the k, k+1 pair)
+    __shared__ __nv_bfloat16 Ah[kBM][kBK + kPad], Al[kBM][kBK + kPad];
+    __shared__ __nv_bfloat16 Bh[kBN][kBK + kPad], Bl[kBN][kBK + kPad];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;   // warp's 32 x 32 sub-tile
+    const int g = lane >> 2, t = lane & 3;                    // fragment row group, thread in group
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += kBK) {
+        for (int e = tid; e < kBM * kBK; e += blockDim.x) {
+            const int r = e / kBK, k = e % kBK, m = m0 + r, kk = k0 + k;
             float a = 0.f;
-            if (m < M && k < K) a = TA_T ? A[(size_t)k * M + m] : A[(size_t)m * K + k];
-            As[r][tx] = a;
-            const int kk = k0 + r, n = blockIdx.x * kTile + tx;
+            if (m < M && kk < K) a = TA_T ? A[(size_t)kk * M + m] : A[(size_t)m * K + kk];
+            const __nv_bfloat16 hi = __float2bfloat16(a);
+            Ah[r][k] = hi;
+            Al[r][k] = __float2bfloat16(a - __bfloat162float(hi));
+        }
+        for (int e = tid; e < kBN * kBK; e += blockDim.x) {
+            const int c = e / kBK, k = e % kBK, n = n0 + c, kk = k0 + k;
             float b = 0.f;
-            if (kk < K && n < N) {
+            if (n < N && kk < K) {
                 if constexpr (TB_T) b = (float)B[(size_t)n * K + kk];
                 else b = (float)B[(size_t)kk * N + n];
             }
-            Bs[r][tx] = b;
+            const __nv_bfloat16 hi = __float2bfloat16(b);
+            Bh[c][k] = hi;
+            if constexpr (kSplitB) Bl[c][k] = __float2bfloat16(b - __bfloat162float(hi));
         }
         __syncthreads();
-#pragma unroll 8
-        for (int k = 0; k < kTile; ++k) {
-            const float b = Bs[k][tx];
+        uint32_t ah[2][4], al[2][4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[i] = fmaf(As[ty + 8 * i][k], b, acc[i]);
+        for (int i = 0; i < 2; ++i) {
+            const int r = wm + 16 * i + g;
+            ah[i][0] = pack_bf16(Ah[r][2 * t], Ah[r][2 * t + 1]);
+            ah[i][1] = pack_bf16(Ah[r + 8][2 * t], Ah[r + 8][2 * t + 1]);
+            ah[i][2] = pack_bf16(Ah[r][2 * t + 8], Ah[r][2 * t + 9]);
+            ah[i][3] = pack_bf16(Ah[r + 8][2 * t + 8], Ah[r + 8][2 * t + 9]);
+            al[i][0] = pack_bf16(Al[r][2 * t], Al[r][2 * t + 1]);
+            al[i][1] = pack_bf16(Al[r + 8][2 * t], Al[r + 8][2 * t + 1]);
+            al[i][2] = pack_bf16(Al[r][2 * t + 8], Al[r][2 * t + 9]);
+            al[i][3] = pack_bf16(Al[r + 8][2 * t + 8], Al[r + 8][2 * t + 9]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = wn + 8 * j + g;
+            const uint32_t bh[2] = {pack_bf16(Bh[c][2 * t], Bh[c][2 * t + 1]),
+                                    pack_bf16(Bh[c][2 * t + 8], Bh[c][2 * t + 9])};
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                mma_bf16(acc[i][j], ah[i], bh);
+                mma_bf16(acc[i][j], al[i], bh);
+            }
+            if constexpr (kSplitB) {
+                const uint32_t bl[2] = {pack_bf16(Bl[c][2 * t], Bl[c][2 * t + 1]),
+                                        pack_bf16(Bl[c][2 * t + 8], Bl[c][2 * t + 9])};
+#pragma unroll
+                for (int i = 0; i < 2; ++i) mma_bf16(acc[i][j], ah[i], bl);
+            }
         }
         __syncthreads();
     }
-    if (col >= N) return;
+    // accumulator element e of the 16 x 8 tile: row g (+8 for e >= 2), column 2t + (e & 1)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int m = row0 + ty + 8 * i;
-        if (m >= M) continue;
-        float v = acc[i];
-        if (bias) v += bias[col];
-        if (relu) v = fmaxf(v, 0.f);
-        float* dst = C + (size_t)m * N + col;
-        *dst = accumulate ? *dst + v : v;
-    }
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int m = m0 + wm + 16 * i + g + (e >= 2 ? 8 : 0);
+                const int n = n0 + wn + 8 * j + 2 * t + (e & 1);
+                if (m >= M || n >= N) continue;
+                float v = acc[i][j][e];
+                if (bias) v += bias[n];
+                if (relu) v = fmaxf(v, 0.f);
+                float* dst = C + (size_t)m * N + n;
+                *dst = accumulate ? *dst + v : v;
+            }
 }
 
 template <typename TB, bool TA_T, bool TB_T>
 void gemm(int M, int N, int K, const float* A, const TB* B, float* C, const float* bias, bool relu, bool accumulate,
           cudaStream_t st) {
-    dim3 block(kTile, 8), grid((N + kTile - 1) / kTile, (M + kTile - 1) / kTile);
+    dim3 block(128), grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM);
     gemm_kernel<TB, TA_T, TB_T><<<grid, block, 0, st>>>(M, N, K, A, B, C, bias, relu ? 1 : 0, accumulate ? 1 : 0);
 }
 
