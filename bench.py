@@ -71,6 +71,9 @@ def parse_args():
                     help="skip the time-to-|dF|<=1e-6 comparison of the batched and plain paths")
     ap.add_argument("--jit", default="auto", choices=["auto", "on", "off"],
                     help="pass-specialised sweep kernels (NQS_OPT_JIT): automatic, always, never")
+    ap.add_argument("--shard", action="store_true",
+                    help="with several GPUs: split one call's terms over the ranks (NQS_OPT_SHARD_*) and merge the "
+                         "level sums (strong scaling) instead of one replica per rank")
     ap.add_argument("--rb", type=int, default=0, choices=[0, 3, 4],
                     help="register qubits of multi-state sweep passes (NQS_OPT_SWEEP_RB; 0 automatic)")
     ap.add_argument("--launch-list", default=None,
@@ -256,11 +259,11 @@ def cpu_model():
     return platform.processor() or platform.machine()
 
 
-def workload_config(args, w, level, desc, n_terms):
+def workload_config(args, w, level, desc, n_terms, shard=False):
     return {"workload": args.workload, "description": desc, "n_qubits": w.n, "gates": len(w.gates),
             "noises": w.n_noise, "level": level, "terms": n_terms, "state_bytes": 8 << w.n,
             "l2": "inputs larger than L2 (8 GiB states)" if w.n >= 25 else "L2-resident states (no flush)",
-            "parallelism": "replicas" if dist_env()[0] > 1 else "single"}
+            "parallelism": ("shards of one call" if shard else "replicas") if dist_env()[0] > 1 else "single"}
 
 
 # ----------------------------------------------------------------------------- distributed
@@ -345,6 +348,10 @@ def run_nqs(args):
     nqs.nqs_set_option(h, nqs.NQS_OPT_JIT, jit_opt)
     if args.rb:
         nqs.nqs_set_option(h, nqs.NQS_OPT_SWEEP_RB, args.rb)
+    shard = args.shard and world > 1
+    if shard:
+        nqs.nqs_set_option(h, nqs.NQS_OPT_SHARD_COUNT, world)
+        nqs.nqs_set_option(h, nqs.NQS_OPT_SHARD_RANK, rank)
     psi, v = nqs.basis(0), (nqs.ideal() if w.v["kind"] == "ideal" else nqs.basis(w.v["bits"]))
     stream = torch.cuda.current_stream()
 
@@ -388,9 +395,12 @@ def run_nqs(args):
     dom, dom_name = (multi, "sweep_kernel, 3-state branch-group passes") if multi["total_ms"] >= single["total_ms"] \
         else (single, "sweep_kernel, single-state passes")
     nqs.nqs_set_profiling(h, 0)
-    t_max, units = aggregate(elapsed, args.steps * n_terms, torch.device("cuda", dev))
+    # replicas: every rank evaluates the whole call; shards: the ranks share one call
+    t_max, units = aggregate(elapsed, args.steps * n_terms / (world if shard else 1), torch.device("cuda", dev))
     value = units / t_max
     res = slot(args.warmup + args.steps - 1).to_dict()
+    if shard:
+        res["T"], res["F"] = nqs.merge_level_sums_distributed(res["T"])
 
     peak, peak_src = measured_peaks()
     achieved = dom["algorithmic_bytes"] / (dom["total_ms"] / 1000.0) / 1e9 if dom["total_ms"] else 0.0
@@ -452,8 +462,8 @@ def run_nqs(args):
         line = {
             "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": workload_config(args, w, level, desc, n_terms),
+            "scaling": "strong" if shard else "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": workload_config(args, w, level, desc, n_terms, shard),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if peak else None, "traffic": traffic,
                          "kernel": dom_name, "peak_source": peak_src,

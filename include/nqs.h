@@ -185,6 +185,14 @@ int nqs_term_values(nqs_handle h, double* out, size_t cap, size_t* count);
  * dropped and dominant parts, Theorem 1's argument per site). */
 int nqs_truncation_bound(nqs_handle h, int level, double* out);
 
+/* The kept terms (canonical order, level `level`) that shard `rank` of
+ * `count` evaluates under NQS_OPT_SHARD_RANK / NQS_OPT_SHARD_COUNT: mask[i]
+ * = 1 for its terms; *n receives the term count (call with mask = NULL or
+ * cap too small for the count only).  Host only.  No counterpart in the
+ * paper (Algorithm 1's outer loops over site sets are independent).
+ * Errors: NQS_ERR_ARG, NQS_ERR_ORDER, NQS_ERR_UNSUPPORTED (general noises). */
+int nqs_shard_mask(nqs_handle h, int level, int rank, int count, uint8_t* mask, size_t cap, size_t* n);
+
 /* Adaptive level selection (Theorem 1 and the level study of Sec. V: the
  * truncation error falls with the level, and a low level usually suffices).
  * The level is raised until the dropped part is below `tol`, judged by
@@ -276,6 +284,13 @@ int nqs_schedule_launches(nqs_handle h, nqs_launch_info* out, size_t cap, size_t
  *       passes: 3 (512-thread blocks) or 4 (256-thread blocks).
  *   NQS_OPT_MAX_OPS       fused operations per pass, 8..160 (default 96).
  *   NQS_OPT_MAX_SITES     noise sites per pass, 1..8 (default 4).
+ *   NQS_OPT_SHARD_RANK, NQS_OPT_SHARD_COUNT   split one call's terms over
+ *       `count` shards (one per GPU): shard `rank` evaluates the level-0/1
+ *       terms when rank = 0 and every term whose first non-dominant site s
+ *       has s mod count = rank; the other terms of its result are zero, so
+ *       the shards' T_u add up to the whole call's (nqs_shard_mask lists a
+ *       shard's terms).  Each shard runs its own backward and forward sweeps.
+ *       0 / 0 (or 1): no split.  A rank >= count is NQS_ERR_ARG at the call.
  *   NQS_OPT_JIT           sweep passes of 12-qubit tiles run kernels generated
  *       for each pass (operations, layouts and matrices compiled in as
  *       constants; NVRTC at schedule build time, cached for the process):
@@ -289,6 +304,8 @@ int nqs_schedule_launches(nqs_handle h, nqs_launch_info* out, size_t cap, size_t
 #define NQS_OPT_MAX_OPS 3
 #define NQS_OPT_MAX_SITES 4
 #define NQS_OPT_JIT 5
+#define NQS_OPT_SHARD_RANK 6
+#define NQS_OPT_SHARD_COUNT 7
 
 int nqs_set_option(nqs_handle h, int option, int64_t value);
 int nqs_get_option(nqs_handle h, int option, int64_t* value);

@@ -166,6 +166,7 @@ int nqs_fidelity(nqs_handle hh, const nqs_state* psi, const nqs_state* v, int le
     }
     int lvl = std::min(level, (int)h->factors.size());
     if (lvl > NQS_MAX_LEVEL) return NQS_ERR_ARG;
+    if (h->opt_shard_rank >= std::max(1, h->opt_shard_count)) return NQS_ERR_ARG;
     return engine_fidelity(*h, psi, v, lvl, out, stream);
 }
 
@@ -275,6 +276,36 @@ int nqs_general_factors(nqs_handle hh, uint32_t site, int32_t* m, int32_t* dim, 
         if (KB) {
             KB[2 * e] = f.KB[e].real();
             KB[2 * e + 1] = f.KB[e].imag();
+        }
+    }
+    return NQS_OK;
+}
+
+int nqs_shard_mask(nqs_handle hh, int level, int rank, int count, uint8_t* mask, size_t cap, size_t* n) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !n || level < 0 || count < 1 || rank < 0 || rank >= count || (cap && !mask)) return NQS_ERR_ARG;
+    if (!h->prepared) return NQS_ERR_ORDER;
+    if (h->general) return NQS_ERR_UNSUPPORTED;
+    const int N = (int)h->factors.size();
+    const int lvl = std::min(level, N);
+    std::vector<int> m(N);
+    for (int s = 0; s < N; ++s) m[s] = h->factors[s].m;
+    TermIndex ti;
+    ti.build(m, lvl);
+    *n = (size_t)ti.total;
+    if (!mask || cap < ti.total) return NQS_OK;
+    for (int u = 0; u <= lvl; ++u) {
+        const uint64_t lo = ti.level_offset[u], hi = ti.level_offset[u + 1];
+        if (u <= 1) {
+            std::memset(mask + lo, rank == 0 ? 1 : 0, hi - lo);
+            continue;
+        }
+        // level u: site tuples in lexicographic order; the first site decides
+        uint64_t at = lo;
+        for (int s = 0; s < N && at < hi; ++s) {
+            const uint64_t cnt = (uint64_t)m[s] * ti.E[u - 1][s + 1];   // tuples starting at s
+            std::memset(mask + at, (s % count == rank) ? 1 : 0, cnt);
+            at += cnt;
         }
     }
     return NQS_OK;
@@ -449,6 +480,14 @@ int nqs_set_option(nqs_handle hh, int option, int64_t value) {
             if (value > 2) return NQS_ERR_ARG;
             h->opt_jit = (int)value;
             break;
+        case NQS_OPT_SHARD_RANK:
+            if (value > 65535) return NQS_ERR_ARG;
+            h->opt_shard_rank = (int)value;
+            break;
+        case NQS_OPT_SHARD_COUNT:
+            if (value > 65536) return NQS_ERR_ARG;
+            h->opt_shard_count = (int)value;
+            break;
         case NQS_OPT_MAX_OPS:
         case NQS_OPT_MAX_SITES: {
             if (!h->prepared) return NQS_ERR_ORDER;
@@ -472,6 +511,8 @@ int nqs_get_option(nqs_handle hh, int option, int64_t* value) {
         case NQS_OPT_CKPT_SPACING: *value = h->opt_spacing; break;
         case NQS_OPT_SWEEP_RB: *value = h->opt_rb_multi; break;
         case NQS_OPT_JIT: *value = h->opt_jit; break;
+        case NQS_OPT_SHARD_RANK: *value = h->opt_shard_rank; break;
+        case NQS_OPT_SHARD_COUNT: *value = h->opt_shard_count; break;
         case NQS_OPT_MAX_OPS: *value = h->opt_max_ops; break;
         case NQS_OPT_MAX_SITES: *value = h->opt_max_sites; break;
         default: return NQS_ERR_ARG;

@@ -540,8 +540,8 @@ struct Builder {
     // (level-0/1 reductions, spawning three states per site), then sweep the
     // block's spawned groups through every later block, recomputing each
     // block's phi once for all of them.
-    template <typename RankFn>
-    void spaced_forward(int k, const float2* ext, RankFn main_rank) {
+    template <typename RankFn, typename OwnFn>
+    void spaced_forward(int k, const float2* ext, RankFn main_rank, OwnFn owns_group) {
         const int N = (int)h.factors.size();
         const int nb = (N + k - 1) / k;
         const Run& fwd0 = run_fwd[0];
@@ -581,7 +581,8 @@ struct Builder {
             const int s_lo = b * k, s_hi = std::min(N, (b + 1) * k);
             for (int c = b; c < nb; ++c) {
                 materialize(c);
-                for (int s = s_lo; s < s_hi; ++s) group_block(s, c, k, b1);
+                for (int s = s_lo; s < s_hi; ++s)
+                    if (owns_group(s)) group_block(s, c, k, b1);
             }
         }
     }
@@ -839,8 +840,13 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
     }
     // finisher ranks of the main forward sweep: level 0 at the first site, level 1 everywhere
     bool first_red = true;
+    // sharding of one call's terms: levels 0 and 1 belong to shard 0, a branch
+    // group (and every deeper term below it) to shard (first site mod count)
+    const int shard_count = std::max(1, h.opt_shard_count), shard_rank = h.opt_shard_rank;
+    auto owns_group = [&](int s) { return s % shard_count == shard_rank; };
     auto main_rank = [&](int t, int s, int i, FinishDesc& d) {
         (void)s;
+        if (shard_rank != 0) return;
         const Factors& ft = h.factors[t];
         if (i == 0) {
             if (first_red) {
@@ -871,7 +877,7 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
                 for (int i = 0; i < 3; ++i) sp.push_back(B.group_bufs[1][i]);
             B.add_pass(rp, 0, 1, in1, out1, sp.empty() ? nullptr : sp.data(), (int)sp.size());
             B.add_finish(rp, 0, 1, main_rank);
-            if (level >= 2 && rp.spawn_site >= 0) {
+            if (level >= 2 && rp.spawn_site >= 0 && owns_group(rp.spawn_site)) {
                 int s = rp.spawn_site;
                 B.dfs_group(1, {}, s, h.factors[s].m, B.group_bufs[1]);
             }
@@ -897,7 +903,7 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
         bool ext = false;
         const float2* ext_ptr = nullptr;
         init_state(psi, mainb, ext, ext_ptr);
-        B.spaced_forward(spacing, ext ? ext_ptr : nullptr, main_rank);
+        B.spaced_forward(spacing, ext ? ext_ptr : nullptr, main_rank, owns_group);
     }
     {
         Launch l;

@@ -153,6 +153,8 @@ struct Handle {
     int opt_max_ops = 0;           // operations per pass (segmentation)
     int opt_max_sites = 0;         // sites per pass (segmentation)
     int opt_jit = 0;               // pass-specialised kernels: 0 auto, 1 always, 2 never
+    int opt_shard_rank = 0;        // this shard of the terms (multi-GPU split of one call)
+    int opt_shard_count = 0;       // 0 or 1: no split
     // general noises: the circuit is evaluated by the general-noise path
     bool general = false;
     std::vector<GFactors> gfac;

@@ -36,6 +36,8 @@ NQS_OPT_SWEEP_RB = 2
 NQS_OPT_MAX_OPS = 3
 NQS_OPT_MAX_SITES = 4
 NQS_OPT_JIT = 5
+NQS_OPT_SHARD_RANK = 6
+NQS_OPT_SHARD_COUNT = 7
 
 
 class NqsError(RuntimeError):
@@ -116,6 +118,8 @@ _SIGS = {
     "nqs_term_values": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t,
                                        ctypes.POINTER(ctypes.c_size_t)]),
     "nqs_truncation_bound": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "nqs_shard_mask": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "nqs_general_factors": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -378,6 +382,51 @@ def nqs_offdiagonal(h, psi, x, y, level, stream=None):
     _check(_lib().nqs_offdiagonal(h, ctypes.byref(ps), ctypes.byref(xs), ctypes.byref(ys), int(level), out, parts,
                                   _stream_ptr(stream)), "nqs_offdiagonal")
     return complex(out[0], out[1]), [parts[k].to_dict() for k in range(4)]
+
+
+def nqs_shard_mask(h, level, rank, count):
+    """Boolean mask over the canonical kept terms: the ones shard `rank` of
+    `count` evaluates (NQS_OPT_SHARD_RANK / NQS_OPT_SHARD_COUNT)."""
+    import numpy as np
+    n = ctypes.c_size_t()
+    _check(_lib().nqs_shard_mask(h, level, rank, count, None, 0, ctypes.byref(n)), "nqs_shard_mask")
+    mask = np.zeros(n.value, np.uint8)
+    _check(_lib().nqs_shard_mask(h, level, rank, count, mask.ctypes.data_as(ctypes.c_void_p), n.value,
+                                 ctypes.byref(n)), "nqs_shard_mask")
+    return mask.astype(bool)
+
+
+def merge_level_sums(parts):
+    """Merge the per-level sums T_u of several shards of one call, in the
+    order given (Neumaier compensation across the shards): the whole call's
+    T_u and F."""
+    L = max(len(p) for p in parts)
+    T = []
+    for u in range(L):
+        s, c = 0.0, 0.0
+        for p in parts:
+            x = p[u] if u < len(p) else 0.0
+            t = s + x
+            c += (s - t) + x if abs(s) >= abs(x) else (x - t) + s
+            s = t
+        T.append(s + c)
+    s, c = 0.0, 0.0
+    for x in T:
+        t = s + x
+        c += (s - t) + x if abs(s) >= abs(x) else (x - t) + s
+        s = t
+    return T, s + c
+
+
+def merge_level_sums_distributed(T, group=None):
+    """All shards of a torch.distributed group exchange their T_u (a few
+    doubles) and merge them in rank order; every rank gets the whole call's
+    (T_u, F)."""
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    parts = [None] * world
+    dist.all_gather_object(parts, list(T), group=group)
+    return merge_level_sums(parts)
 
 
 def nqs_general_factors(h, site):
