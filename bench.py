@@ -392,8 +392,9 @@ def run_nqs(args):
     fills = nqs.nqs_get_kernel_stats(h, 2)
     multi = nqs.nqs_get_kernel_stats(h, 3)    # branch-group passes (several states)
     single = nqs.nqs_get_kernel_stats(h, 4)   # single-state passes
-    dom, dom_name = (multi, "sweep_kernel, 3-state branch-group passes") if multi["total_ms"] >= single["total_ms"] \
-        else (single, "sweep_kernel, single-state passes")
+    kname = "nqs_pass (generated per pass)" if nqs.nqs_get_info(h)["jit_launches"] > 0 else "sweep_kernel"
+    dom, dom_name = (multi, kname + ", 3-state branch-group passes") if multi["total_ms"] >= single["total_ms"] \
+        else (single, kname + ", single-state passes")
     nqs.nqs_set_profiling(h, 0)
     # replicas: every rank evaluates the whole call; shards: the ranks share one call
     t_max, units = aggregate(elapsed, args.steps * n_terms / (world if shard else 1), torch.device("cuda", dev))

@@ -45,6 +45,13 @@ static bool jit_env_enabled() {
     return !(e && e[0] == '0');
 }
 
+// multi-state generated passes sweep their states one at a time (NQS_JIT_SEQ=0:
+// all states in registers together)
+static bool jit_seq_enabled() {
+    const char* e = std::getenv("NQS_JIT_SEQ");
+    return !(e && e[0] == '0');
+}
+
 
 
 // Program of one register-resident launch, appended to `prog` (16-byte
@@ -371,7 +378,10 @@ struct Builder {
             l.args.out[s] = out[s];
         }
         for (int i = 0; i < n_spawn; ++i) l.args.spawn[i] = spawn[i];
-        l.grid = grid_for(S, l.rb, l.args.n_tiles, l.args.prog_words, l.args.n_events);
+        l.seq = rt && use_jit && S > 1 && jit_seq_enabled();
+        // state-sequential generated passes: two 256-thread blocks per SM
+        l.grid = l.seq ? (int)std::max<long long>(1, std::min<long long>(2ll * E.sm_count, l.args.n_tiles))
+                       : grid_for(S, l.rb, l.args.n_tiles, l.args.prog_words, l.args.n_events);
         l.smem = (size_t)S * (1 << plan.k) * sizeof(float2);
         partial_doubles = std::max(partial_doubles, (size_t)std::max(1, l.args.n_events) * S * l.grid * 8);
         // algorithmic bytes: state load + store, phi reads, checkpoint and spawn writes
@@ -922,6 +932,7 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
             if (l.kind != L_PASS || !l.rt) continue;
             std::unique_ptr<JitPass> jp(new JitPass());
             jp->S = l.S;
+            jp->seq = l.seq;
             jp->RB = l.rb;
             jp->n = plan.n;
             for (int j = 0; j < kMaxTileQ; ++j) jp->local[j] = l.args.local[j];

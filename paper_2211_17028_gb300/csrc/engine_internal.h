@@ -53,6 +53,7 @@ struct Launch {
     bool bd_table = false;           // pass saves through the block-boundary checkpoint table
     int op_counts[8] = {};           // pass: G1, G2, D1, D2, sites, reductions, spawned states, saves
     JitPass* jit = nullptr;          // pass-specialised kernel (owned by the engine), or the interpreter
+    bool seq = false;                // multi-state pass-specialised kernel sweeps its states one at a time
 };
 
 struct Engine {

@@ -200,6 +200,11 @@ struct Gen {
     const JitPass& J;
     std::ostringstream o;
     int S, RB, E, NT, NW, WB;
+    // SEQ: the S states of a multi-state pass are swept one after another
+    // through the same code (one state in registers, runtime state index st);
+    // SS is the number of states, S the states held in registers
+    bool SEQ = false;
+    int SS = 1;
     // layout of the current phase
     int R[4] = {}, Lp[5] = {}, Wp[4] = {};
     int ph = 0;
@@ -221,7 +226,9 @@ struct Gen {
     }
 
     explicit Gen(const JitPass& j) : J(j) {
-        S = J.S;
+        SS = J.S;
+        SEQ = J.seq && J.S > 1;
+        S = SEQ ? 1 : J.S;
         RB = J.RB;
         E = 1 << RB;
         NT = 4096 >> RB;
@@ -244,6 +251,12 @@ struct Gen {
     }
 
     std::string name(const char* p) { return std::string(p) + std::to_string(tmp++); }
+
+    bool has_spawn() const {
+        for (const OpRec& op : J.ops)
+            if (op.type == 5 && (op.flags & 2)) return true;
+        return false;
+    }
 
     void set_phase(int p) {
         ph = p;
@@ -680,7 +693,7 @@ struct Gen {
             } else {
                 o << "    float2 ph[" << E << "];\n";
                 o << "    const float2* const pp = phi" << (int)op.ev << " + gb;\n";
-                emit_gather("ph", "pp", true);
+                emit_gather("ph", "pp", !SEQ);   // the other states re-read phi from L2
             }
             for (int s = 0; s < S; ++s) {
                 o << "    { float2 R00 = make_float2(0.f, 0.f), R01 = R00, R10 = R00, R11 = R00;\n";
@@ -696,7 +709,7 @@ struct Gen {
                       << kargs(sc) << ", R10); R11 = mulK(" << kargs(sc) << ", R11);\n";
                 o << "      const float w[8] = {R00.x, R00.y, R01.x, R01.y, R10.x, R10.y, R11.x, R11.y};\n";
                 o << "      const float v = warp_rs8(w, lane);\n";
-                o << "      if ((lane & 3) == 0) acc[((" << (int)op.ev << " * " << S << " + " << s << ") * " << NW
+                o << "      if ((lane & 3) == 0) acc[((" << (int)op.ev << " * " << SS << " + " << (SEQ ? std::string("st") : std::to_string(s)) << ") * " << NW
                   << " + warp) * 8 + ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] += (double)v;\n";
                 o << "    }\n";
             }
@@ -707,7 +720,10 @@ struct Gen {
                 for (int k = 0; k < ns; ++k) {
                     const cd K[4] = {m[4 * (k + 1)] * sc, m[4 * (k + 1) + 1] * sc, m[4 * (k + 1) + 2] * sc,
                                      m[4 * (k + 1) + 3] * sc};
-                    o << "    { float2* const dp = P.spawn[" << s * 3 + k << "] + gb;\n";
+                    if (SEQ)
+                        o << "    { float2* const dp = spw" << k << " + gb;\n";
+                    else
+                        o << "    { float2* const dp = P.spawn[" << s * 3 + k << "] + gb;\n";
                     // value of amplitude r of K x: rows by the site's bit
                     emit_scatter("dp", [&](int r) {
                         const int r0 = r & ~(1 << i), r1 = r | 1 << i;
@@ -750,7 +766,7 @@ struct Gen {
         o << "  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;\n";
         o << "  const int cta = blockIdx.x, nctas = gridDim.x;\n";
         o << "  (void)lane; (void)warp;\n";
-        o << "  for (int i = tid; i < " << J.n_events * S * NW * 8 << "; i += " << NT << ") acc[i] = 0.0;\n";
+        o << "  for (int i = tid; i < " << J.n_events * SS * NW * 8 << "; i += " << NT << ") acc[i] = 0.0;\n";
         o << "  if (tid == 0) { mbar_init(&bar, 1); asm volatile(\"fence.mbarrier_init.release.cluster;\" ::: \"memory\"); }\n";
         o << "  __syncthreads();\n";
         for (int p = 0; p < n_ph; ++p) {
@@ -771,11 +787,27 @@ struct Gen {
         o << "  auto hi_off = [&](int h) -> u64 { return 0ull";
         for (int j = 0; j < 7; ++j) o << " | ((u64)((h >> " << j << ") & 1) << " << J.local[5 + j] << ")";
         o << "; };\n";
-        o << "  auto prefetch = [&](u64 bb) {\n";
-        o << "    asm volatile(\"fence.proxy.async.shared::cta;\" ::: \"memory\");\n";
-        o << "    if (tid == 0) mbar_arrive_expect_tx(&bar, " << S * 4096 * 8 << "u);\n";
-        o << "    for (int q = tid; q < " << S * 128 << "; q += " << NT << ") { const int s = q >> 7, h = q & 127; "
-             "bulk_g2s(pf + s * KT + h * 32, P.in[s] + (bb | hi_off(h)), 256u, &bar); }\n";
+        // state selection by the runtime index st (SEQ)
+        auto pick = [&](const std::string& arr, int stride, int k) {
+            std::string e = arr + "[" + std::to_string((SS - 1) * stride + k) + "]";
+            for (int q = SS - 2; q >= 0; --q)
+                e = "(st == " + std::to_string(q) + " ? " + arr + "[" + std::to_string(q * stride + k) + "] : " + e + ")";
+            return e;
+        };
+        if (SEQ) {
+            o << "  auto prefetch = [&](u64 bb, int st) {\n";
+            o << "    asm volatile(\"fence.proxy.async.shared::cta;\" ::: \"memory\");\n";
+            o << "    if (tid == 0) mbar_arrive_expect_tx(&bar, " << 4096 * 8 << "u);\n";
+            o << "    const float2* const src = " << pick("P.in", 1, 0) << ";\n";
+            o << "    for (int h = tid; h < 128; h += " << NT << ") bulk_g2s(pf + h * 32, src + (bb | hi_off(h)), 256u, &bar);\n";
+            o << "    if (st != 0) return;\n";
+        } else {
+            o << "  auto prefetch = [&](u64 bb) {\n";
+            o << "    asm volatile(\"fence.proxy.async.shared::cta;\" ::: \"memory\");\n";
+            o << "    if (tid == 0) mbar_arrive_expect_tx(&bar, " << S * 4096 * 8 << "u);\n";
+            o << "    for (int q = tid; q < " << S * 128 << "; q += " << NT << ") { const int s = q >> 7, h = q & 127; "
+                 "bulk_g2s(pf + s * KT + h * 32, P.in[s] + (bb | hi_off(h)), 256u, &bar); }\n";
+        }
         if (J.n_events > 0) {
             o << "    for (int q = tid; q < " << J.n_events * 128 << "; q += " << NT << ") { const int e = q >> 7, h = q & 127; "
                  "const float2* ph = ";
@@ -784,15 +816,30 @@ struct Gen {
         }
         o << "  };\n";
         o << "  long long t = cta;\n";
-        o << "  if (t < P.n_tiles) prefetch(base);\n";
+        if (SEQ) {
+            o << "  int st = 0;\n";
+            o << "  if (t < P.n_tiles) prefetch(base, 0);\n";
+        } else {
+            o << "  if (t < P.n_tiles) prefetch(base);\n";
+        }
         o << "  u32 parity = 0;\n  bool failed = false;\n";
         o << "  float2 x[" << S << "][" << E << "];\n";
         o << "  float2 dsc = make_float2(1.f, 0.f);\n";
         for (int i = 0; i < RB; ++i) o << "  float2 dh" << i << "_0 = dsc, dh" << i << "_1 = dsc;\n";
         o << "  (void)dsc;\n";
         for (int i = 0; i < RB; ++i) o << "  (void)dh" << i << "_0; (void)dh" << i << "_1;\n";
-        o << "  for (; t < P.n_tiles; t += nctas) {\n";
-        o << "    const u64 b = base;\n";
+        if (SEQ) {
+            // (tile, state) pairs: the states of a tile one after another, so
+            // the tile's phi values are read from DRAM once and from L2 after
+            o << "  #pragma unroll 1\n";
+            o << "  while (t < P.n_tiles) {\n";
+            o << "    const u64 b = base;\n";
+            o << "    u64 nbase = base;\n    long long nt = t;\n    int nst = st + 1;\n";
+            o << "    if (nst == " << SS << ") { nst = 0; nt = t + nctas; nbase = ((base | ~NL) + step) & NL; }\n";
+        } else {
+            o << "  for (; t < P.n_tiles; t += nctas) {\n";
+            o << "    const u64 b = base;\n";
+        }
         o << "    const bool ok = mbar_wait(&bar, parity);\n";
         o << "    if (__syncthreads_or(!ok)) { failed = true; break; }\n";
         o << "    parity ^= 1u;\n";
@@ -802,7 +849,15 @@ struct Gen {
             for (int r = 0; r < E; ++r)
                 o << "    x[" << s << "][" << r << "] = pf[" << s * 4096 + jr(J.phases[0], r) << " + jT0];\n";
         o << "    __syncthreads();\n";
-        o << "    if (t + nctas < P.n_tiles) { base = ((base | ~NL) + step) & NL; prefetch(base); }\n";
+        if (SEQ) {
+            o << "    if (nt < P.n_tiles) prefetch(nbase, nst);\n";
+            if (J.n_events > 0 || has_spawn()) {
+                for (int k = 0; k < 3; ++k)
+                    if (has_spawn()) o << "    float2* const spw" << k << " = " << pick("P.spawn", 3, k) << ";\n";
+            }
+        } else {
+            o << "    if (t + nctas < P.n_tiles) { base = ((base | ~NL) + step) & NL; prefetch(base); }\n";
+        }
         for (int p = 0; p < n_ph; ++p) {
             if (p > 0) {
                 // re-layout through the swizzled buffer
@@ -834,7 +889,7 @@ struct Gen {
                     --budget;
                     o << "    float2 phe" << (int)op.ev << "[" << E << "];\n";
                     o << "    { const float2* const pp = phi" << (int)op.ev << " + (b | gT" << p << ");\n";
-                    emit_gather("phe" + std::to_string((int)op.ev), "pp", true);
+                    emit_gather("phe" + std::to_string((int)op.ev), "pp", !SEQ);
                     o << "    }\n";
                 }
             }
@@ -859,11 +914,15 @@ struct Gen {
         // store the tile
         o << "    {\n";
         for (int s = 0; s < S; ++s) {
-            o << "    { float2* const op = P.out[" << s << "] + (b | gT" << n_ph - 1 << ");\n";
+            if (SEQ)
+                o << "    { float2* const op = " << pick("P.out", 1, 0) << " + (b | gT" << n_ph - 1 << ");\n";
+            else
+                o << "    { float2* const op = P.out[" << s << "] + (b | gT" << n_ph - 1 << ");\n";
             emit_scatter("op", [&](int r) { return "x[" + std::to_string(s) + "][" + std::to_string(r) + "]"; });
             o << "    }\n";
         }
         o << "    }\n";
+        if (SEQ) o << "    t = nt; base = nbase; st = nst;\n";
         o << "  }\n";
         o << "  if (failed) {\n";
         o << "    if (tid == 0) atomicExch(P.err, " << J.err_timeout << ");\n";
@@ -872,11 +931,11 @@ struct Gen {
         o << "  }\n";
         if (J.n_events > 0) {
             o << "  __syncthreads();\n";
-            o << "  for (int i = tid; i < " << J.n_events * S * 8 << "; i += " << NT << ") {\n";
-            o << "    const int e = i & 7, s = (i >> 3) % " << S << ", ev = (i >> 3) / " << S << ";\n";
+            o << "  for (int i = tid; i < " << J.n_events * SS * 8 << "; i += " << NT << ") {\n";
+            o << "    const int e = i & 7, s = (i >> 3) % " << SS << ", ev = (i >> 3) / " << SS << ";\n";
             o << "    double v = 0.0;\n";
-            o << "    for (int w = 0; w < " << NW << "; ++w) v += acc[((ev * " << S << " + s) * " << NW << " + w) * 8 + e];\n";
-            o << "    P.partials[((size_t)(ev * " << S << " + s) * nctas + cta) * 8 + e] = v;\n";
+            o << "    for (int w = 0; w < " << NW << "; ++w) v += acc[((ev * " << SS << " + s) * " << NW << " + w) * 8 + e];\n";
+            o << "    P.partials[((size_t)(ev * " << SS << " + s) * nctas + cta) * 8 + e] = v;\n";
             o << "  }\n";
         }
         o << "}\n";
@@ -1075,7 +1134,8 @@ int jit_build(std::vector<JitPass*>& passes, std::string* error) {
 
 size_t JitPass::smem_bytes() const {
     const int NT = 4096 >> RB, NW = NT / 32;
-    return (size_t)S * 4096 * 16 + (size_t)n_events * S * NW * 8 * sizeof(double);
+    const int held = (seq && S > 1) ? 1 : S;   // state tiles in shared memory (staging + re-layout)
+    return (size_t)held * 4096 * 16 + (size_t)n_events * S * NW * 8 * sizeof(double);
 }
 
 cudaError_t jit_launch(const JitPass& p, int grid, const PassArgs& a, cudaStream_t st) {

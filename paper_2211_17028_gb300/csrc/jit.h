@@ -13,6 +13,7 @@ namespace nqs {
 // Everything the generator needs from one register-resident launch.
 struct JitPass {
     int S = 1, RB = 4, n = 0;
+    bool seq = false;         // multi-state pass swept one state at a time (2 blocks per SM)
     int local[kMaxTileQ] = {};
     int nonlocal[kMaxQ] = {};
     int n_events = 0;
