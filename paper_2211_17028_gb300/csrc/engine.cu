@@ -52,6 +52,12 @@ static bool jit_seq_enabled() {
     return !(e && e[0] == '0');
 }
 
+// staging buffers of the generated kernels that hold one state in registers
+static int jit_staging_buffers() {
+    const char* e = std::getenv("NQS_JIT_DB");
+    return (e && e[0] == '2') ? 2 : 1;
+}
+
 
 
 // Program of one register-resident launch, appended to `prog` (16-byte
@@ -380,8 +386,10 @@ struct Builder {
         for (int i = 0; i < n_spawn; ++i) l.args.spawn[i] = spawn[i];
         l.seq = rt && use_jit && S > 1 && jit_seq_enabled();
         // state-sequential generated passes: two 256-thread blocks per SM
-        l.grid = l.seq ? (int)std::max<long long>(1, std::min<long long>(2ll * E.sm_count, l.args.n_tiles))
-                       : grid_for(S, l.rb, l.args.n_tiles, l.args.prog_words, l.args.n_events);
+        l.grid = (l.seq || (rt && use_jit && S == 1))
+                     ? (int)std::max<long long>(1, std::min<long long>((long long)jit_blocks_per_sm() * E.sm_count,
+                                                                       l.args.n_tiles))
+                     : grid_for(S, l.rb, l.args.n_tiles, l.args.prog_words, l.args.n_events);
         l.smem = (size_t)S * (1 << plan.k) * sizeof(float2);
         partial_doubles = std::max(partial_doubles, (size_t)std::max(1, l.args.n_events) * S * l.grid * 8);
         // algorithmic bytes: state load + store, phi reads, checkpoint and spawn writes
@@ -933,6 +941,7 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
             std::unique_ptr<JitPass> jp(new JitPass());
             jp->S = l.S;
             jp->seq = l.seq;
+            jp->db = jit_staging_buffers();
             jp->RB = l.rb;
             jp->n = plan.n;
             for (int j = 0; j < kMaxTileQ; ++j) jp->local[j] = l.args.local[j];

@@ -160,6 +160,20 @@ static __device__ __forceinline__ float warp_rs8(const float (&w)[8], int lane) 
 )PRELUDE";
 
 // ------------------------------------------------------------------ code generation
+}  // namespace
+
+// resident blocks per SM of the kernels that hold one state in registers
+int jit_blocks_per_sm() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = std::getenv("NQS_JIT_MINB");
+        v = (e && (e[0] == '2' || e[0] == '3')) ? e[0] - '0' : 2;
+    }
+    return v;
+}
+
+namespace {
+
 bool flush_rt_enabled() {
     static int v = -1;
     if (v < 0) {
@@ -754,20 +768,25 @@ struct Gen {
             if (op.type == 5 && (op.flags & 1)) red_sites[op.ev] = op.site;
         unsigned long long nl_mask = 0;
         for (int j = 0; j < J.n - 12; ++j) nl_mask |= 1ull << J.nonlocal[j];
-        const int minb = S == 1 ? 2 : 1;
+        const int minb = S == 1 ? jit_blocks_per_sm() : 1;
         o << kPrelude;
         o << "extern \"C\" __global__ void __launch_bounds__(" << NT << ", " << minb
           << ") nqs_pass(const JitArgs P) {\n";
         o << "  extern __shared__ __align__(128) unsigned char dyn[];\n";
+        // kernels holding one state in registers (one state, or SEQ) stage
+        // their tiles through a ring of DB buffers, one mbarrier each
+        const bool ONE = (S == 1);
+        const int DB = ONE ? std::max(1, std::min(2, J.db)) : 1;
         o << "  float2* const pf = (float2*)dyn;\n";
-        o << "  float2* const tr = pf + " << S << " * KT;\n";
+        o << "  float2* const tr = pf + " << (ONE ? DB : S) << " * KT;\n";
         o << "  double* const acc = (double*)(tr + " << S << " * KT);\n";
-        o << "  __shared__ __align__(8) u64 bar;\n";
+        o << "  __shared__ __align__(8) u64 bar[" << DB << "];\n";
         o << "  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;\n";
         o << "  const int cta = blockIdx.x, nctas = gridDim.x;\n";
         o << "  (void)lane; (void)warp;\n";
         o << "  for (int i = tid; i < " << J.n_events * SS * NW * 8 << "; i += " << NT << ") acc[i] = 0.0;\n";
-        o << "  if (tid == 0) { mbar_init(&bar, 1); asm volatile(\"fence.mbarrier_init.release.cluster;\" ::: \"memory\"); }\n";
+        o << "  if (tid == 0) { for (int i = 0; i < " << DB << "; ++i) mbar_init(&bar[i], 1); "
+             "asm volatile(\"fence.mbarrier_init.release.cluster;\" ::: \"memory\"); }\n";
         o << "  __syncthreads();\n";
         for (int p = 0; p < n_ph; ++p) {
             o << "  const int jT" << p << " = " << jt_expr(J.phases[p]) << ";\n";
@@ -794,19 +813,20 @@ struct Gen {
                 e = "(st == " + std::to_string(q) + " ? " + arr + "[" + std::to_string(q * stride + k) + "] : " + e + ")";
             return e;
         };
-        if (SEQ) {
-            o << "  auto prefetch = [&](u64 bb, int st) {\n";
+        if (ONE) {
+            o << "  auto prefetch = [&](u64 bb, int st, int buf) {\n";
             o << "    asm volatile(\"fence.proxy.async.shared::cta;\" ::: \"memory\");\n";
-            o << "    if (tid == 0) mbar_arrive_expect_tx(&bar, " << 4096 * 8 << "u);\n";
+            o << "    if (tid == 0) mbar_arrive_expect_tx(&bar[buf], " << 4096 * 8 << "u);\n";
             o << "    const float2* const src = " << pick("P.in", 1, 0) << ";\n";
-            o << "    for (int h = tid; h < 128; h += " << NT << ") bulk_g2s(pf + h * 32, src + (bb | hi_off(h)), 256u, &bar);\n";
+            o << "    float2* const dst = pf + buf * KT;\n";
+            o << "    for (int h = tid; h < 128; h += " << NT << ") bulk_g2s(dst + h * 32, src + (bb | hi_off(h)), 256u, &bar[buf]);\n";
             o << "    if (st != 0) return;\n";
         } else {
             o << "  auto prefetch = [&](u64 bb) {\n";
             o << "    asm volatile(\"fence.proxy.async.shared::cta;\" ::: \"memory\");\n";
-            o << "    if (tid == 0) mbar_arrive_expect_tx(&bar, " << S * 4096 * 8 << "u);\n";
+            o << "    if (tid == 0) mbar_arrive_expect_tx(&bar[0], " << S * 4096 * 8 << "u);\n";
             o << "    for (int q = tid; q < " << S * 128 << "; q += " << NT << ") { const int s = q >> 7, h = q & 127; "
-                 "bulk_g2s(pf + s * KT + h * 32, P.in[s] + (bb | hi_off(h)), 256u, &bar); }\n";
+                 "bulk_g2s(pf + s * KT + h * 32, P.in[s] + (bb | hi_off(h)), 256u, &bar[0]); }\n";
         }
         if (J.n_events > 0) {
             o << "    for (int q = tid; q < " << J.n_events * 128 << "; q += " << NT << ") { const int e = q >> 7, h = q & 127; "
@@ -816,46 +836,58 @@ struct Gen {
         }
         o << "  };\n";
         o << "  long long t = cta;\n";
-        if (SEQ) {
-            o << "  int st = 0;\n";
-            o << "  if (t < P.n_tiles) prefetch(base, 0);\n";
+        if (ONE) {
+            // consumer cursor (t, base, st), producer cursor (pt, pbase, pst)
+            o << "  int st = 0;\n  (void)st;\n";
+            o << "  long long pt = t;\n  u64 pbase = base;\n  int pst = 0;\n";
+            o << "  u32 par = 0u, infl = 0u;\n  int cb = 0;\n";
+            o << "  for (int i = 0; i < " << DB << "; ++i) if (pt < P.n_tiles) { prefetch(pbase, pst, i); infl |= 1u << i; "
+                 "if (++pst == " << SS << ") { pst = 0; pt += nctas; pbase = ((pbase | ~NL) + step) & NL; } }\n";
+            o << "  bool failed = false;\n";
         } else {
             o << "  if (t < P.n_tiles) prefetch(base);\n";
+            o << "  u32 parity = 0;\n  bool failed = false;\n";
         }
-        o << "  u32 parity = 0;\n  bool failed = false;\n";
         o << "  float2 x[" << S << "][" << E << "];\n";
         o << "  float2 dsc = make_float2(1.f, 0.f);\n";
         for (int i = 0; i < RB; ++i) o << "  float2 dh" << i << "_0 = dsc, dh" << i << "_1 = dsc;\n";
         o << "  (void)dsc;\n";
         for (int i = 0; i < RB; ++i) o << "  (void)dh" << i << "_0; (void)dh" << i << "_1;\n";
-        if (SEQ) {
-            // (tile, state) pairs: the states of a tile one after another, so
-            // the tile's phi values are read from DRAM once and from L2 after
+        if (ONE) {
+            // (tile, state) pairs; with several states (SEQ) the states of a
+            // tile follow one another, so the tile's phi values are read from
+            // DRAM once and from L2 for the other states
             o << "  #pragma unroll 1\n";
             o << "  while (t < P.n_tiles) {\n";
             o << "    const u64 b = base;\n";
-            o << "    u64 nbase = base;\n    long long nt = t;\n    int nst = st + 1;\n";
-            o << "    if (nst == " << SS << ") { nst = 0; nt = t + nctas; nbase = ((base | ~NL) + step) & NL; }\n";
+            o << "    const bool ok = mbar_wait(&bar[cb], (par >> cb) & 1u);\n";
+            o << "    if (__syncthreads_or(!ok)) { failed = true; break; }\n";
+            o << "    par ^= 1u << cb;\n    infl &= ~(1u << cb);\n";
+            set_phase(0);
+            o << "    { const float2* const cur = pf + cb * KT;\n";
+            for (int r = 0; r < E; ++r)
+                o << "    x[0][" << r << "] = cur[" << jr(J.phases[0], r) << " + jT0];\n";
+            o << "    }\n";
+            o << "    __syncthreads();\n";
+            o << "    if (pt < P.n_tiles) { prefetch(pbase, pst, cb); infl |= 1u << cb; "
+                 "if (++pst == " << SS << ") { pst = 0; pt += nctas; pbase = ((pbase | ~NL) + step) & NL; } }\n";
         } else {
             o << "  for (; t < P.n_tiles; t += nctas) {\n";
             o << "    const u64 b = base;\n";
+            o << "    const bool ok = mbar_wait(&bar[0], parity);\n";
+            o << "    if (__syncthreads_or(!ok)) { failed = true; break; }\n";
+            o << "    parity ^= 1u;\n";
+            // load phase 0 from the staging buffer
+            set_phase(0);
+            for (int s = 0; s < S; ++s)
+                for (int r = 0; r < E; ++r)
+                    o << "    x[" << s << "][" << r << "] = pf[" << s * 4096 + jr(J.phases[0], r) << " + jT0];\n";
+            o << "    __syncthreads();\n";
         }
-        o << "    const bool ok = mbar_wait(&bar, parity);\n";
-        o << "    if (__syncthreads_or(!ok)) { failed = true; break; }\n";
-        o << "    parity ^= 1u;\n";
-        // load phase 0 from the staging buffer
-        set_phase(0);
-        for (int s = 0; s < S; ++s)
-            for (int r = 0; r < E; ++r)
-                o << "    x[" << s << "][" << r << "] = pf[" << s * 4096 + jr(J.phases[0], r) << " + jT0];\n";
-        o << "    __syncthreads();\n";
         if (SEQ) {
-            o << "    if (nt < P.n_tiles) prefetch(nbase, nst);\n";
-            if (J.n_events > 0 || has_spawn()) {
-                for (int k = 0; k < 3; ++k)
-                    if (has_spawn()) o << "    float2* const spw" << k << " = " << pick("P.spawn", 3, k) << ";\n";
-            }
-        } else {
+            if (has_spawn())
+                for (int k = 0; k < 3; ++k) o << "    float2* const spw" << k << " = " << pick("P.spawn", 3, k) << ";\n";
+        } else if (!ONE) {
             o << "    if (t + nctas < P.n_tiles) { base = ((base | ~NL) + step) & NL; prefetch(base); }\n";
         }
         for (int p = 0; p < n_ph; ++p) {
@@ -922,11 +954,17 @@ struct Gen {
             o << "    }\n";
         }
         o << "    }\n";
-        if (SEQ) o << "    t = nt; base = nbase; st = nst;\n";
+        if (ONE) {
+            o << "    if (++st == " << SS << ") { st = 0; t += nctas; base = ((base | ~NL) + step) & NL; }\n";
+            o << "    cb = (cb + 1 == " << DB << ") ? 0 : cb + 1;\n";
+        }
         o << "  }\n";
         o << "  if (failed) {\n";
         o << "    if (tid == 0) atomicExch(P.err, " << J.err_timeout << ");\n";
-        o << "    mbar_wait(&bar, parity);\n";
+        if (ONE)   // the copies still in flight land before the block exits
+            o << "    for (int i = 0; i < " << DB << "; ++i) if ((infl >> i) & 1u) mbar_wait(&bar[i], (par >> i) & 1u);\n";
+        else
+            o << "    mbar_wait(&bar[0], parity);\n";
         o << "    return;\n";
         o << "  }\n";
         if (J.n_events > 0) {
@@ -1134,8 +1172,11 @@ int jit_build(std::vector<JitPass*>& passes, std::string* error) {
 
 size_t JitPass::smem_bytes() const {
     const int NT = 4096 >> RB, NW = NT / 32;
-    const int held = (seq && S > 1) ? 1 : S;   // state tiles in shared memory (staging + re-layout)
-    return (size_t)held * 4096 * 16 + (size_t)n_events * S * NW * 8 * sizeof(double);
+    // one state in registers: a ring of db staging tiles and one re-layout
+    // tile; otherwise a staging and a re-layout tile per state
+    const bool one = S == 1 || seq;
+    const size_t tiles = one ? (size_t)std::max(1, std::min(2, db)) + 1 : (size_t)2 * S;
+    return tiles * 4096 * 8 + (size_t)n_events * S * NW * 8 * sizeof(double);
 }
 
 cudaError_t jit_launch(const JitPass& p, int grid, const PassArgs& a, cudaStream_t st) {

@@ -13,6 +13,7 @@ namespace nqs {
 // Everything the generator needs from one register-resident launch.
 struct JitPass {
     int S = 1, RB = 4, n = 0;
+    int db = 1;               // staging buffers of one-state kernels (1 or 2)
     bool seq = false;         // multi-state pass swept one state at a time (2 blocks per SM)
     int local[kMaxTileQ] = {};
     int nonlocal[kMaxQ] = {};
@@ -40,6 +41,7 @@ struct JitArgsHost {
 
 std::string jit_source(const JitPass& p);
 bool jit_available();
+int jit_blocks_per_sm();      // resident blocks per SM of one-state-in-registers kernels
 long long jit_compile_count();
 // Generate, compile (distinct sources in parallel, cached for the process)
 // and load every pass; 0 on success, -1 with a message otherwise.
