@@ -52,6 +52,26 @@ static bool jit_seq_enabled() {
     return !(e && e[0] == '0');
 }
 
+// two re-layout buffers in the generated one-state kernels (NQS_JIT_PP=0: one)
+static bool jit_pingpong() {
+    const char* e = std::getenv("NQS_JIT_PP");
+    return !(e && e[0] == '0');
+}
+
+// L2 eviction policies of the generated kernels (NQS_JIT_HINT bits, default 3:
+// state tiles evict-first, phi kept in L2 until the last state of a tile read it)
+static int jit_hint() {
+    const char* e = std::getenv("NQS_JIT_HINT");
+    return e ? (std::atoi(e) & 3) : 3;
+}
+
+// site reduction form of the generated kernels (NQS_JIT_RV=1: conjugate
+// multiply-add per product; default 2: split accumulators, no swapped operands)
+static int jit_reduction_form() {
+    const char* e = std::getenv("NQS_JIT_RV");
+    return (e && e[0] == '1') ? 1 : 2;
+}
+
 // staging buffers of the generated kernels that hold one state in registers
 static int jit_staging_buffers() {
     const char* e = std::getenv("NQS_JIT_DB");
@@ -942,6 +962,9 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
             jp->S = l.S;
             jp->seq = l.seq;
             jp->db = jit_staging_buffers();
+            jp->pp = jit_pingpong();
+            jp->hint = jit_hint();
+            jp->rv = jit_reduction_form();
             jp->RB = l.rb;
             jp->n = plan.n;
             for (int j = 0; j < kMaxTileQ; ++j) jp->local[j] = l.args.local[j];

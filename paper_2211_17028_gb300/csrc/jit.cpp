@@ -78,6 +78,35 @@ static __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, u32 
 static __device__ __forceinline__ void bulk_l2(const void* src, u32 bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
+// L2 eviction policies and the copies / loads that carry them
+static __device__ __forceinline__ u64 pol_first() {
+    u64 p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+static __device__ __forceinline__ u64 pol_last() {
+    u64 p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+static __device__ __forceinline__ void bulk_g2s_h(void* dst, const void* src, u32 bytes, u64* bar, u64 pol) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol) : "memory");
+}
+static __device__ __forceinline__ void bulk_l2_h(const void* src, u32 bytes, u64 pol) {
+    asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(src), "r"(bytes), "l"(pol) : "memory");
+}
+static __device__ __forceinline__ float4 ld4_h(const float2* p, u64 pol) {
+    float4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(pol));
+    return v;
+}
+static __device__ __forceinline__ float2 ld2_h(const float2* p, u64 pol) {
+    float2 v;
+    asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
 static __device__ __forceinline__ bool mbar_try(u64* bar, u32 parity) {
     u32 ok;
     asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -122,6 +151,13 @@ static __device__ __forceinline__ float2 cjfma(float2 f, float2 a, float2 acc) {
     acc = __ffma2_rn(make_float2(f.x, f.x), a, acc);
     return __ffma2_rn(make_float2(f.y, -f.y), sw(a), acc);
 }
+// conj(f) * a accumulated as A += f.x * a, B += f.y * a (no swapped or negated
+// operands); conj(f) a = (A.x + B.y, A.y - B.x)
+static __device__ __forceinline__ void cjacc(float2 f, float2 a, float2& A, float2& B) {
+    A = __ffma2_rn(make_float2(f.x, f.x), a, A);
+    B = __ffma2_rn(make_float2(f.y, f.y), a, B);
+}
+static __device__ __forceinline__ float2 cjfin(float2 A, float2 B) { return make_float2(A.x + B.y, A.y - B.x); }
 static __device__ __forceinline__ float2 sel(int c, float2 a, float2 b) { return c ? b : a; }
 // reduce-scatter of 8 floats over a warp; lane l ends with the warp sum of
 // component ((l>>4)&1)*4 + ((l>>3)&1)*2 + ((l>>2)&1) in the return value
@@ -219,6 +255,7 @@ struct Gen {
     // SS is the number of states, S the states held in registers
     bool SEQ = false;
     int SS = 1;
+    bool PP = false;   // two re-layout buffers (one-state kernels)
     // layout of the current phase
     int R[4] = {}, Lp[5] = {}, Wp[4] = {};
     int ph = 0;
@@ -329,9 +366,20 @@ struct Gen {
     // pairs (r, r | 1 << v) with v the register bit of qubit 0 move as float4
     void emit_gather(const std::string& dst, const std::string& ptr, bool stream) {
         const int v = bit_of_q0();
+        const bool hinted = (J.hint & 2) && !stream;   // phi loads with the L2 policy polphi
         for (int r = 0; r < E; ++r) {
             if (v >= 0 && (r >> v & 1)) continue;
             const std::string off = std::to_string(gr(r)) + "ull";
+            if (hinted) {
+                if (v >= 0) {
+                    const int r1 = r | 1 << v;
+                    o << "    { const float4 q = ld4_h(" << ptr << " + " << off << ", polphi); " << dst << "[" << r
+                      << "] = make_float2(q.x, q.y); " << dst << "[" << r1 << "] = make_float2(q.z, q.w); }\n";
+                } else {
+                    o << "    " << dst << "[" << r << "] = ld2_h(" << ptr << " + " << off << ", polphi);\n";
+                }
+                continue;
+            }
             if (v >= 0) {
                 const int r1 = r | 1 << v;
                 o << "    { const float4 q = " << (stream ? "__ldcs" : "__ldg") << "((const float4*)(" << ptr << " + "
@@ -707,16 +755,31 @@ struct Gen {
             } else {
                 o << "    float2 ph[" << E << "];\n";
                 o << "    const float2* const pp = phi" << (int)op.ev << " + gb;\n";
-                emit_gather("ph", "pp", !SEQ);   // the other states re-read phi from L2
+                emit_gather("ph", "pp", !SEQ && !(J.hint & 2));   // the other states re-read phi from L2
             }
             for (int s = 0; s < S; ++s) {
                 o << "    { float2 R00 = make_float2(0.f, 0.f), R01 = R00, R10 = R00, R11 = R00;\n";
-                for (int r = 0; r < E; ++r) {
-                    if (r >> i & 1) continue;
-                    const int r1 = r | 1 << i;
-                    o << "      R00 = cjfma(ph[" << r << "], x[" << s << "][" << r << "], R00); R01 = cjfma(ph[" << r
-                      << "], x[" << s << "][" << r1 << "], R01); R10 = cjfma(ph[" << r1 << "], x[" << s << "][" << r
-                      << "], R10); R11 = cjfma(ph[" << r1 << "], x[" << s << "][" << r1 << "], R11);\n";
+                if (J.rv == 2) {
+                    o << "      float2 A00 = R00, B00 = R00, A01 = R00, B01 = R00, A10 = R00, B10 = R00, A11 = R00, B11 = R00;\n";
+                    for (int r = 0; r < E; ++r) {
+                        if (r >> i & 1) continue;
+                        const int r1 = r | 1 << i;
+                        const std::string f0 = "ph[" + std::to_string(r) + "]", f1 = "ph[" + std::to_string(r1) + "]";
+                        const std::string x0 = "x[" + std::to_string(s) + "][" + std::to_string(r) + "]";
+                        const std::string x1 = "x[" + std::to_string(s) + "][" + std::to_string(r1) + "]";
+                        o << "      cjacc(" << f0 << ", " << x0 << ", A00, B00); cjacc(" << f0 << ", " << x1
+                          << ", A01, B01); cjacc(" << f1 << ", " << x0 << ", A10, B10); cjacc(" << f1 << ", " << x1
+                          << ", A11, B11);\n";
+                    }
+                    o << "      R00 = cjfin(A00, B00); R01 = cjfin(A01, B01); R10 = cjfin(A10, B10); R11 = cjfin(A11, B11);\n";
+                } else {
+                    for (int r = 0; r < E; ++r) {
+                        if (r >> i & 1) continue;
+                        const int r1 = r | 1 << i;
+                        o << "      R00 = cjfma(ph[" << r << "], x[" << s << "][" << r << "], R00); R01 = cjfma(ph[" << r
+                          << "], x[" << s << "][" << r1 << "], R01); R10 = cjfma(ph[" << r1 << "], x[" << s << "][" << r
+                          << "], R10); R11 = cjfma(ph[" << r1 << "], x[" << s << "][" << r1 << "], R11);\n";
+                    }
                 }
                 if (!is_one(sc))
                     o << "      R00 = mulK(" << kargs(sc) << ", R00); R01 = mulK(" << kargs(sc) << ", R01); R10 = mulK("
@@ -777,9 +840,10 @@ struct Gen {
         // their tiles through a ring of DB buffers, one mbarrier each
         const bool ONE = (S == 1);
         const int DB = ONE ? std::max(1, std::min(2, J.db)) : 1;
+        PP = ONE && J.pp;
         o << "  float2* const pf = (float2*)dyn;\n";
         o << "  float2* const tr = pf + " << (ONE ? DB : S) << " * KT;\n";
-        o << "  double* const acc = (double*)(tr + " << S << " * KT);\n";
+        o << "  double* const acc = (double*)(tr + " << (PP ? 2 : S) << " * KT);\n";
         o << "  __shared__ __align__(8) u64 bar[" << DB << "];\n";
         o << "  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;\n";
         o << "  const int cta = blockIdx.x, nctas = gridDim.x;\n";
@@ -806,6 +870,11 @@ struct Gen {
         o << "  auto hi_off = [&](int h) -> u64 { return 0ull";
         for (int j = 0; j < 7; ++j) o << " | ((u64)((h >> " << j << ") & 1) << " << J.local[5 + j] << ")";
         o << "; };\n";
+        if (J.hint) {
+            o << "  const u64 pol_ef = pol_first(), pol_el = pol_last();\n";
+            o << "  const u64 polst = pol_ef;\n  const u64 polpf = " << (SS > 1 ? "pol_el" : "pol_ef") << ";\n";
+            o << "  (void)polst; (void)polpf;\n";
+        }
         // state selection by the runtime index st (SEQ)
         auto pick = [&](const std::string& arr, int stride, int k) {
             std::string e = arr + "[" + std::to_string((SS - 1) * stride + k) + "]";
@@ -819,7 +888,10 @@ struct Gen {
             o << "    if (tid == 0) mbar_arrive_expect_tx(&bar[buf], " << 4096 * 8 << "u);\n";
             o << "    const float2* const src = " << pick("P.in", 1, 0) << ";\n";
             o << "    float2* const dst = pf + buf * KT;\n";
-            o << "    for (int h = tid; h < 128; h += " << NT << ") bulk_g2s(dst + h * 32, src + (bb | hi_off(h)), 256u, &bar[buf]);\n";
+            if (J.hint & 1)
+                o << "    for (int h = tid; h < 128; h += " << NT << ") bulk_g2s_h(dst + h * 32, src + (bb | hi_off(h)), 256u, &bar[buf], polst);\n";
+            else
+                o << "    for (int h = tid; h < 128; h += " << NT << ") bulk_g2s(dst + h * 32, src + (bb | hi_off(h)), 256u, &bar[buf]);\n";
             o << "    if (st != 0) return;\n";
         } else {
             o << "  auto prefetch = [&](u64 bb) {\n";
@@ -832,7 +904,10 @@ struct Gen {
             o << "    for (int q = tid; q < " << J.n_events * 128 << "; q += " << NT << ") { const int e = q >> 7, h = q & 127; "
                  "const float2* ph = ";
             for (int e = 0; e < J.n_events; ++e) o << (e + 1 < J.n_events ? "e == " + std::to_string(e) + " ? phi" + std::to_string(e) + " : " : "phi" + std::to_string(e));
-            o << "; bulk_l2(ph + (bb | hi_off(h)), 256u); }\n";
+            if (J.hint & 2)
+                o << "; bulk_l2_h(ph + (bb | hi_off(h)), 256u, polpf); }\n";
+            else
+                o << "; bulk_l2(ph + (bb | hi_off(h)), 256u); }\n";
         }
         o << "  };\n";
         o << "  long long t = cta;\n";
@@ -863,6 +938,7 @@ struct Gen {
             o << "    const bool ok = mbar_wait(&bar[cb], (par >> cb) & 1u);\n";
             o << "    if (__syncthreads_or(!ok)) { failed = true; break; }\n";
             o << "    par ^= 1u << cb;\n    infl &= ~(1u << cb);\n";
+            if (J.hint) o << "    const u64 polphi = st == " << SS - 1 << " ? pol_ef : pol_el;\n    (void)polphi;\n";
             set_phase(0);
             o << "    { const float2* const cur = pf + cb * KT;\n";
             for (int r = 0; r < E; ++r)
@@ -895,17 +971,21 @@ struct Gen {
                 // re-layout through the swizzled buffer
                 const DevPhase& a = J.phases[p - 1];
                 const DevPhase& c = J.phases[p];
+                // PP: consecutive re-layouts alternate between two buffers, so
+                // the barrier of the next re-layout (or of the next tile) already
+                // orders this one's reads before the buffer is written again
+                const int tb = PP ? ((p - 1) & 1) * 4096 : 0;
                 for (int s = 0; s < S; ++s)
                     for (int r = 0; r < E; ++r)
-                        o << "    tr[" << s * 4096 << " + (sT" << p - 1 << " ^ " << swz(jr(a, r)) << ")] = x[" << s << "]["
-                          << r << "];\n";
+                        o << "    tr[" << tb + s * 4096 << " + (sT" << p - 1 << " ^ " << swz(jr(a, r)) << ")] = x[" << s
+                          << "][" << r << "];\n";
                 o << "    __syncthreads();\n";
                 set_phase(p);
                 for (int s = 0; s < S; ++s)
                     for (int r = 0; r < E; ++r)
-                        o << "    x[" << s << "][" << r << "] = tr[" << s * 4096 << " + (sT" << p << " ^ " << swz(jr(c, r))
-                          << ")];\n";
-                o << "    __syncthreads();\n";
+                        o << "    x[" << s << "][" << r << "] = tr[" << tb + s * 4096 << " + (sT" << p << " ^ "
+                          << swz(jr(c, r)) << ")];\n";
+                if (!PP) o << "    __syncthreads();\n";
             }
             const DevPhase& d = J.phases[p];
             // the phi values of this phase's reductions are loaded at the start
@@ -921,7 +1001,7 @@ struct Gen {
                     --budget;
                     o << "    float2 phe" << (int)op.ev << "[" << E << "];\n";
                     o << "    { const float2* const pp = phi" << (int)op.ev << " + (b | gT" << p << ");\n";
-                    emit_gather("phe" + std::to_string((int)op.ev), "pp", !SEQ);
+                    emit_gather("phe" + std::to_string((int)op.ev), "pp", !SEQ && !(J.hint & 2));
                     o << "    }\n";
                 }
             }
@@ -1175,7 +1255,7 @@ size_t JitPass::smem_bytes() const {
     // one state in registers: a ring of db staging tiles and one re-layout
     // tile; otherwise a staging and a re-layout tile per state
     const bool one = S == 1 || seq;
-    const size_t tiles = one ? (size_t)std::max(1, std::min(2, db)) + 1 : (size_t)2 * S;
+    const size_t tiles = one ? (size_t)std::max(1, std::min(2, db)) + (pp ? 2 : 1) : (size_t)2 * S;
     return tiles * 4096 * 8 + (size_t)n_events * S * NW * 8 * sizeof(double);
 }
 

@@ -13,6 +13,9 @@ namespace nqs {
 // Everything the generator needs from one register-resident launch.
 struct JitPass {
     int S = 1, RB = 4, n = 0;
+    bool pp = false;          // one-state kernels: two re-layout buffers, one barrier per re-layout
+    int hint = 0;             // L2 policies: 1 state tiles evict-first, 2 phi kept for the other states
+    int rv = 1;               // site reduction form: 1 conj-multiply-add, 2 split accumulators
     int db = 1;               // staging buffers of one-state kernels (1 or 2)
     bool seq = false;         // multi-state pass swept one state at a time (2 blocks per SM)
     int local[kMaxTileQ] = {};
