@@ -72,6 +72,23 @@ static int jit_reduction_form() {
     return (e && e[0] == '1') ? 1 : 2;
 }
 
+// 13-qubit tiles for the generated kernels (NQS_JIT_WIDE=1)
+static bool jit_wide_enabled() {
+    const char* e = std::getenv("NQS_JIT_WIDE");
+    return e && e[0] == '1';
+}
+
+// the handle's plan re-cut into passes of 13-qubit tiles, with the handle's
+// segmentation options (the operation order is the same for every tile width)
+static void make_wide_plan(const Handle& h, Plan& w) {
+    w = h.plan;
+    w.k = std::min(h.plan.n, kWideTileQ);
+    const int sites = h.opt_max_sites > 0 ? h.opt_max_sites : 4;
+    const int ops = h.opt_max_ops > 0 ? h.opt_max_ops : 96;
+    w.free_passes = segment(w, false, sites, ops);
+    w.sitecut_passes = segment(w, true, sites, ops);
+}
+
 // staging buffers of the generated kernels that hold one state in registers
 static int jit_staging_buffers() {
     const char* e = std::getenv("NQS_JIT_DB");
@@ -93,8 +110,7 @@ static int jit_staging_buffers() {
 
 
 ProgInfo build_program(const std::vector<DevOp>& dops, int off, int n, int RB, const Tables& tab,
-                       std::vector<uint4>& prog) {
-    const int k = kMaxTileQ;
+                       std::vector<uint4>& prog, int k) {
     const int WB = k - RB - 5;
     std::vector<std::pair<int, int>> ranges;
     std::vector<std::vector<int>> regs;
@@ -157,7 +173,7 @@ ProgInfo build_program(const std::vector<DevOp>& dops, int off, int n, int RB, c
         for (int q = 0; q < k; ++q)
             if (!used[q]) warps.push_back(q);
         DevPhase ph{};
-        int loc[kMaxTileQ];
+        int loc[kTileSlots];
         for (int i = 0; i < RB; ++i) {
             ph.R[i] = (signed char)R[i];
             loc[R[i]] = i;
@@ -325,7 +341,7 @@ struct Builder {
     Run run_ideal, run_bwd, run_mat;   // run_mat: per-block phi recomputation (spaced checkpoints)
     std::vector<Run> run_fwd;    // per depth
 
-    Builder(Handle& hh, Engine& ee, int lvl) : h(hh), E(ee), plan(hh.plan), level(lvl) {
+    Builder(Handle& hh, Engine& ee, int lvl, const Plan& pl) : h(hh), E(ee), plan(pl), level(lvl) {
         dim = 1ll << plan.n;
         const int N = (int)hh.factors.size();
         if (N > 0) {
@@ -370,7 +386,7 @@ struct Builder {
         a.k = rp.k;
         a.c = rp.c;
         a.n_events = (int)rp.ev_site.size();
-        for (int j = 0; j < kMaxTileQ; ++j) a.local[j] = rp.local[j];
+        for (int j = 0; j < kTileSlots; ++j) a.local[j] = rp.local[j];
         for (int j = 0; j < kMaxQ; ++j) a.nonlocal[j] = rp.nonlocal[j];
         a.n_tiles = 1ll << (plan.n - rp.k);
         a.ckpt = ckpt_dev;
@@ -389,26 +405,34 @@ struct Builder {
         if (rt) {
             // pass-specialised multi-state passes hold 16 amplitudes per state and
             // thread (more work per instruction stream, registers for early phi loads)
-            l.rb = (S > 1 && h.opt_rb_multi) ? h.opt_rb_multi : (S > 1 && use_jit) ? 4 : sweep_reg_bits(S);
-            ProgInfo pi = build_program(dops, rp.op_off + start, rp.n_ops - start, l.rb, tab, prog);
+            l.rb = plan.k == kWideTileQ ? 4
+                   : (S > 1 && h.opt_rb_multi) ? h.opt_rb_multi : (S > 1 && use_jit) ? 4 : sweep_reg_bits(S);
+            ProgInfo pi = build_program(dops, rp.op_off + start, rp.n_ops - start, l.rb, tab, prog, plan.k);
             l.prog_index = pi.words_begin;
             l.args.prog_words = pi.n_words;
             l.args.ops_word = pi.ops_word;
             l.args.mats_word = pi.mats_word;
             l.args.n_phases = pi.n_phases;
-            // static shared memory of the kernel stays below 4 KiB
-            if (sweep_smem_bytes(S, l.rb, pi.n_words, l.args.n_events) + 4096 > E.smem_optin) too_big = true;
+            // static shared memory of the kernel stays below 4 KiB (13-qubit tiles:
+            // staging and two re-layout tiles of 64 KiB and the reduction slots)
+            if (plan.k == kWideTileQ) {
+                if ((size_t)3 * (8 << kWideTileQ) + (size_t)l.args.n_events * S * 16 * 64 + 4096 > E.smem_optin)
+                    too_big = true;
+            } else if (sweep_smem_bytes(S, l.rb, pi.n_words, l.args.n_events) + 4096 > E.smem_optin) {
+                too_big = true;
+            }
         }
         for (int s = 0; s < S; ++s) {
             l.args.in[s] = in[s];
             l.args.out[s] = out[s];
         }
         for (int i = 0; i < n_spawn; ++i) l.args.spawn[i] = spawn[i];
-        l.seq = rt && use_jit && S > 1 && jit_seq_enabled();
-        // state-sequential generated passes: two 256-thread blocks per SM
+        l.seq = rt && use_jit && S > 1 && (jit_seq_enabled() || plan.k == kWideTileQ);
+        // state-sequential generated passes: two 256-thread blocks per SM (13-qubit
+        // tiles: one 512-thread block)
+        const long long per_sm = plan.k == kWideTileQ ? 1 : jit_blocks_per_sm();
         l.grid = (l.seq || (rt && use_jit && S == 1))
-                     ? (int)std::max<long long>(1, std::min<long long>((long long)jit_blocks_per_sm() * E.sm_count,
-                                                                       l.args.n_tiles))
+                     ? (int)std::max<long long>(1, std::min<long long>(per_sm * E.sm_count, l.args.n_tiles))
                      : grid_for(S, l.rb, l.args.n_tiles, l.args.prog_words, l.args.n_events);
         l.smem = (size_t)S * (1 << plan.k) * sizeof(float2);
         partial_doubles = std::max(partial_doubles, (size_t)std::max(1, l.args.n_events) * S * l.grid * 8);
@@ -676,24 +700,29 @@ static int best_spacing(int N, int level) {
 // Build (or reuse) the schedule for this level and state kinds.
 int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* v, int level, void* stream,
                    bool allow_jit) {
-    const Plan& plan = h.plan;
     const int N = (int)h.factors.size();
     // automatic: circuits of 26 qubits or more, where one call's sweeps outlast
     // the compilation of its distinct passes
     const bool want_jit =
-        allow_jit && (h.opt_jit == 1 || (h.opt_jit == 0 && plan.n >= 26 && jit_env_enabled()));
+        allow_jit && (h.opt_jit == 1 || (h.opt_jit == 0 && h.plan.n >= 26 && jit_env_enabled()));
     if (E.level == level && E.psi_kind == psi->kind && E.v_kind == v->kind && E.psi_bits == psi->bits &&
         E.v_bits == v->bits && E.psi_dev == psi->dev && E.v_dev == v->dev && !(want_jit && E.jit_state == 0))
         return NQS_OK;
     engine_release(E, stream);
     ++E.gen;
 
-    Builder B(h, E, level);
+    // generated kernels may sweep 13-qubit tiles (fewer passes); if their
+    // kernels cannot be built the schedule is rebuilt for 12-qubit tiles
+    E.wide = want_jit && !E.wide_failed && h.plan.k == kMaxTileQ && h.plan.n > kWideTileQ && jit_wide_enabled() &&
+             jit_available();
+    if (E.wide) make_wide_plan(h, E.wide_plan);
+    const Plan& plan = E.wide ? E.wide_plan : h.plan;
+    Builder B(h, E, level, plan);
     std::vector<int> m(N);
     for (int s = 0; s < N; ++s) m[s] = h.factors[s].m;
     B.ti.build(m, level);
 
-    B.rt = plan.k == kMaxTileQ;
+    B.rt = plan.k == kMaxTileQ || E.wide;
     B.use_jit = want_jit && B.rt && jit_available();
     if (want_jit && B.rt && !B.use_jit) E.jit_state = -1;   // NVRTC missing: the interpreting kernel runs
     // finisher factor table (complex128)
@@ -960,6 +989,7 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
             if (l.kind != L_PASS || !l.rt) continue;
             std::unique_ptr<JitPass> jp(new JitPass());
             jp->S = l.S;
+            jp->k = plan.k;
             jp->seq = l.seq;
             jp->db = jit_staging_buffers();
             jp->pp = jit_pingpong();
@@ -967,7 +997,7 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
             jp->rv = jit_reduction_form();
             jp->RB = l.rb;
             jp->n = plan.n;
-            for (int j = 0; j < kMaxTileQ; ++j) jp->local[j] = l.args.local[j];
+            for (int j = 0; j < kTileSlots; ++j) jp->local[j] = l.args.local[j];
             for (int j = 0; j < kMaxQ; ++j) jp->nonlocal[j] = l.args.nonlocal[j];
             jp->n_events = l.args.n_events;
             const uint4* w = B.prog.data() + l.prog_index;
@@ -990,6 +1020,11 @@ int build_schedule(Handle& h, Engine& E, const nqs_state* psi, const nqs_state* 
             E.jit.clear();
             E.jit_state = todo.empty() ? 0 : -1;
             if (!todo.empty() && std::getenv("NQS_JIT_VERBOSE")) std::fprintf(stderr, "nqs jit: %s\n", err.c_str());
+            if (E.wide) {   // the interpreting kernel needs 12-qubit tiles
+                E.wide_failed = true;
+                engine_release(E, stream);
+                return build_schedule(h, E, psi, v, level, stream, allow_jit);
+            }
         }
     }
 

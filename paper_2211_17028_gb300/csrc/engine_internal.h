@@ -18,7 +18,7 @@ namespace nqs {
 struct RunPass {
     int op_off = 0, n_ops = 0;       // in the device op buffer
     int k = 0, c = 0;
-    int local[kMaxTileQ] = {};
+    int local[kTileSlots] = {};
     int nonlocal[kMaxQ] = {};
     std::vector<int> lin;            // linear op index of each device op
     std::vector<int> ev_site;        // site of reduction event e
@@ -98,6 +98,9 @@ struct Engine {
     std::vector<std::unique_ptr<JitPass>> jit;   // pass-specialised kernels of the current schedule
     int jit_launches = 0;
     int jit_state = 0;               // 0 not requested, 1 built, -1 failed (interpreter runs)
+    Plan wide_plan;                  // the plan re-cut for 13-qubit tiles (generated kernels)
+    bool wide = false;               // the current schedule runs on wide_plan
+    bool wide_failed = false;        // a wide schedule's kernels could not be built: 12-qubit tiles
 };
 
 
@@ -127,7 +130,7 @@ struct ProgInfo {
 
 int cuda_err(cudaError_t e);
 ProgInfo build_program(const std::vector<DevOp>& dops, int off, int n, int RB, const Tables& tab,
-                       std::vector<uint4>& prog);
+                       std::vector<uint4>& prog, int k = kMaxTileQ);
 // Device ops of one sweep direction over the passes `segs`.  Backward runs
 // save phi at every site, or only at the sites flagged in `save_only`.
 Run make_run(const Plan& plan, const std::vector<PassSpec>& segs, RunType rt, bool reduce, bool spawn,

@@ -77,6 +77,68 @@ std::array<cd, 16> matmul(const std::array<cd, 16>& a, const std::array<cd, 16>&
 
 bool op_is_diag(const HostOp& o) { return o.type == OP_D1 || o.type == OP_D2; }
 
+// Reorders the operations so that in-order segmentation needs fewer passes.
+// Pass by pass, every remaining operation is taken (in order) when its dense
+// qubits still fit the tile and it commutes with every operation skipped before
+// it in this pass: two operations commute when they share no qubit or are both
+// diagonal.  A noise site commutes with nothing on its qubit (the branch states
+// it spawns and the reduction it makes see the state at its place), and sites
+// keep their relative order.  The reordered product of operations equals the
+// original one.
+void lookahead_order(Plan& p, int max_sites, int max_ops) {
+    const int nops = (int)p.ops.size();
+    std::vector<int> rest(nops), order;
+    for (int i = 0; i < nops; ++i) rest[i] = i;
+    order.reserve(nops);
+    while (!rest.empty()) {
+        std::vector<char> in(p.n, 0), blk_diag(p.n, 0), blk_any(p.n, 0);
+        int count = 0;
+        for (int q = 0; q < p.c; ++q) {
+            in[q] = 1;
+            ++count;
+        }
+        bool site_skipped = false;
+        int sites = 0, taken = 0;
+        std::vector<int> keep;
+        for (int idx : rest) {
+            const HostOp& o = p.ops[idx];
+            const int qs[2] = {o.q0, o.q1};
+            const int nq = o.q1 >= 0 ? 2 : 1;
+            const bool d = op_is_diag(o), site = o.type == OP_SITE;
+            bool ok = !(site && site_skipped) && taken < max_ops && !(site && sites >= max_sites);
+            for (int j = 0; j < nq && ok; ++j)
+                if (blk_any[qs[j]] || (!d && blk_diag[qs[j]])) ok = false;
+            int extra = 0;
+            if (!d)
+                for (int j = 0; j < nq; ++j)
+                    if (!in[qs[j]] && !(j == 1 && qs[1] == qs[0])) ++extra;
+            if (count + extra > p.k) ok = false;
+            if (ok) {
+                if (!d)
+                    for (int j = 0; j < nq; ++j)
+                        if (!in[qs[j]]) {
+                            in[qs[j]] = 1;
+                            ++count;
+                        }
+                sites += site;
+                ++taken;
+                order.push_back(idx);
+            } else {
+                for (int j = 0; j < nq; ++j) (d ? blk_diag : blk_any)[qs[j]] = 1;
+                site_skipped = site_skipped || site;
+                keep.push_back(idx);
+            }
+        }
+        rest.swap(keep);
+    }
+    std::vector<HostOp> ops;
+    ops.reserve(nops);
+    for (int idx : order) ops.push_back(p.ops[idx]);
+    p.ops.swap(ops);
+    for (int i = 0; i < nops; ++i)
+        if (p.ops[i].type == OP_SITE) p.site_pos[p.ops[i].site] = i;
+}
+
 }  // namespace
 
 void build_plan(const Circuit& c, const std::vector<Factors>& f, int tile_qubits, Plan& p) {
@@ -216,6 +278,7 @@ void build_plan(const Circuit& c, const std::vector<Factors>& f, int tile_qubits
                 for (int cc = 0; cc < 4; ++cc)
                     if (r != cc) o.m[4 * r + cc] = cd(0);
     }
+    lookahead_order(p, 4, 96);
     // bounded passes: at most 4 reductions and 96 operations each, so a pass's
     // program and reduction slots fit next to the tiles in shared memory
     p.free_passes = segment(p, false, 4, 96);

@@ -62,7 +62,6 @@ struct JitArgs {
     int* err;
     long long n_tiles;
 };
-#define KT 4096
 #define SPIN_LIMIT (1 << 19)
 static __device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
 static __device__ __forceinline__ void mbar_init(u64* bar, int count) {
@@ -250,6 +249,7 @@ struct Gen {
     const JitPass& J;
     std::ostringstream o;
     int S, RB, E, NT, NW, WB;
+    int K = 12, KT = 4096, CH = 128;   // tile qubits, amplitudes per tile, 256-byte chunks per tile
     // SEQ: the S states of a multi-state pass are swept one after another
     // through the same code (one state in registers, runtime state index st);
     // SS is the number of states, S the states held in registers
@@ -282,9 +282,12 @@ struct Gen {
         S = SEQ ? 1 : J.S;
         RB = J.RB;
         E = 1 << RB;
-        NT = 4096 >> RB;
+        K = J.k;
+        KT = 1 << K;
+        CH = 1 << (K - 5);
+        NT = KT >> RB;
         NW = NT / 32;
-        WB = 12 - RB - 5;
+        WB = K - RB - 5;
         T.assign(E, 1.0);
         reset_pending();
     }
@@ -323,7 +326,7 @@ struct Gen {
             if (r >> i & 1) j |= 1 << d.R[i];
         return j;
     }
-    static int swz(int j) { return j ^ ((j >> 4) & 15) ^ ((j >> 8) & 15); }
+    static int swz(int j) { return j ^ ((j >> 4) & 15) ^ ((j >> 8) & 15) ^ ((j >> 12) & 15); }
     unsigned long long gr(int r) const {
         unsigned long long g = 0;
         for (int i = 0; i < RB; ++i)
@@ -830,9 +833,12 @@ struct Gen {
         for (const OpRec& op : J.ops)
             if (op.type == 5 && (op.flags & 1)) red_sites[op.ev] = op.site;
         unsigned long long nl_mask = 0;
-        for (int j = 0; j < J.n - 12; ++j) nl_mask |= 1ull << J.nonlocal[j];
-        const int minb = S == 1 ? jit_blocks_per_sm() : 1;
+        for (int j = 0; j < J.n - K; ++j) nl_mask |= 1ull << J.nonlocal[j];
+        // one-state kernels of 12-qubit tiles: several 256-thread blocks per SM;
+        // 13-qubit tiles: one 512-thread block
+        const int minb = (S == 1 && K == 12) ? jit_blocks_per_sm() : 1;
         o << kPrelude;
+        o << "#define KT " << KT << "\n";
         o << "extern \"C\" __global__ void __launch_bounds__(" << NT << ", " << minb
           << ") nqs_pass(const JitArgs P) {\n";
         o << "  extern __shared__ __align__(128) unsigned char dyn[];\n";
@@ -855,7 +861,7 @@ struct Gen {
         for (int p = 0; p < n_ph; ++p) {
             o << "  const int jT" << p << " = " << jt_expr(J.phases[p]) << ";\n";
             o << "  const int sT" << p << " = jT" << p << " ^ ((jT" << p << " >> 4) & 15) ^ ((jT" << p
-              << " >> 8) & 15);\n";
+              << " >> 8) & 15) ^ ((jT" << p << " >> 12) & 15);\n";
             o << "  const u64 gT" << p << " = " << gt_expr(J.phases[p]) << ";\n";
             o << "  (void)jT" << p << "; (void)sT" << p << "; (void)gT" << p << ";\n";
         }
@@ -868,7 +874,7 @@ struct Gen {
              "if (v & 1) step |= low; if (w & 1) base |= low; v >>= 1; w >>= 1; m ^= low; } }\n";
         // chunk offsets: bits 5..11 of the tile index on qubits local[5..11]
         o << "  auto hi_off = [&](int h) -> u64 { return 0ull";
-        for (int j = 0; j < 7; ++j) o << " | ((u64)((h >> " << j << ") & 1) << " << J.local[5 + j] << ")";
+        for (int j = 0; j < K - 5; ++j) o << " | ((u64)((h >> " << j << ") & 1) << " << J.local[5 + j] << ")";
         o << "; };\n";
         if (J.hint) {
             o << "  const u64 pol_ef = pol_first(), pol_el = pol_last();\n";
@@ -885,23 +891,25 @@ struct Gen {
         if (ONE) {
             o << "  auto prefetch = [&](u64 bb, int st, int buf) {\n";
             o << "    asm volatile(\"fence.proxy.async.shared::cta;\" ::: \"memory\");\n";
-            o << "    if (tid == 0) mbar_arrive_expect_tx(&bar[buf], " << 4096 * 8 << "u);\n";
+            o << "    if (tid == 0) mbar_arrive_expect_tx(&bar[buf], " << KT * 8 << "u);\n";
             o << "    const float2* const src = " << pick("P.in", 1, 0) << ";\n";
             o << "    float2* const dst = pf + buf * KT;\n";
             if (J.hint & 1)
-                o << "    for (int h = tid; h < 128; h += " << NT << ") bulk_g2s_h(dst + h * 32, src + (bb | hi_off(h)), 256u, &bar[buf], polst);\n";
+                o << "    for (int h = tid; h < " << CH << "; h += " << NT << ") bulk_g2s_h(dst + h * 32, src + (bb | hi_off(h)), 256u, &bar[buf], polst);\n";
             else
-                o << "    for (int h = tid; h < 128; h += " << NT << ") bulk_g2s(dst + h * 32, src + (bb | hi_off(h)), 256u, &bar[buf]);\n";
+                o << "    for (int h = tid; h < " << CH << "; h += " << NT << ") bulk_g2s(dst + h * 32, src + (bb | hi_off(h)), 256u, &bar[buf]);\n";
             o << "    if (st != 0) return;\n";
         } else {
             o << "  auto prefetch = [&](u64 bb) {\n";
             o << "    asm volatile(\"fence.proxy.async.shared::cta;\" ::: \"memory\");\n";
-            o << "    if (tid == 0) mbar_arrive_expect_tx(&bar[0], " << S * 4096 * 8 << "u);\n";
-            o << "    for (int q = tid; q < " << S * 128 << "; q += " << NT << ") { const int s = q >> 7, h = q & 127; "
+            o << "    if (tid == 0) mbar_arrive_expect_tx(&bar[0], " << S * KT * 8 << "u);\n";
+            o << "    for (int q = tid; q < " << S * CH << "; q += " << NT << ") { const int s = q >> " << K - 5
+              << ", h = q & " << CH - 1 << "; "
                  "bulk_g2s(pf + s * KT + h * 32, P.in[s] + (bb | hi_off(h)), 256u, &bar[0]); }\n";
         }
         if (J.n_events > 0) {
-            o << "    for (int q = tid; q < " << J.n_events * 128 << "; q += " << NT << ") { const int e = q >> 7, h = q & 127; "
+            o << "    for (int q = tid; q < " << J.n_events * CH << "; q += " << NT << ") { const int e = q >> " << K - 5
+              << ", h = q & " << CH - 1 << "; "
                  "const float2* ph = ";
             for (int e = 0; e < J.n_events; ++e) o << (e + 1 < J.n_events ? "e == " + std::to_string(e) + " ? phi" + std::to_string(e) + " : " : "phi" + std::to_string(e));
             if (J.hint & 2)
@@ -957,7 +965,7 @@ struct Gen {
             set_phase(0);
             for (int s = 0; s < S; ++s)
                 for (int r = 0; r < E; ++r)
-                    o << "    x[" << s << "][" << r << "] = pf[" << s * 4096 + jr(J.phases[0], r) << " + jT0];\n";
+                    o << "    x[" << s << "][" << r << "] = pf[" << s * KT + jr(J.phases[0], r) << " + jT0];\n";
             o << "    __syncthreads();\n";
         }
         if (SEQ) {
@@ -974,16 +982,16 @@ struct Gen {
                 // PP: consecutive re-layouts alternate between two buffers, so
                 // the barrier of the next re-layout (or of the next tile) already
                 // orders this one's reads before the buffer is written again
-                const int tb = PP ? ((p - 1) & 1) * 4096 : 0;
+                const int tb = PP ? ((p - 1) & 1) * KT : 0;
                 for (int s = 0; s < S; ++s)
                     for (int r = 0; r < E; ++r)
-                        o << "    tr[" << tb + s * 4096 << " + (sT" << p - 1 << " ^ " << swz(jr(a, r)) << ")] = x[" << s
+                        o << "    tr[" << tb + s * KT << " + (sT" << p - 1 << " ^ " << swz(jr(a, r)) << ")] = x[" << s
                           << "][" << r << "];\n";
                 o << "    __syncthreads();\n";
                 set_phase(p);
                 for (int s = 0; s < S; ++s)
                     for (int r = 0; r < E; ++r)
-                        o << "    x[" << s << "][" << r << "] = tr[" << tb + s * 4096 << " + (sT" << p << " ^ "
+                        o << "    x[" << s << "][" << r << "] = tr[" << tb + s * KT << " + (sT" << p << " ^ "
                           << swz(jr(c, r)) << ")];\n";
                 if (!PP) o << "    __syncthreads();\n";
             }
@@ -1251,12 +1259,12 @@ int jit_build(std::vector<JitPass*>& passes, std::string* error) {
 }
 
 size_t JitPass::smem_bytes() const {
-    const int NT = 4096 >> RB, NW = NT / 32;
+    const int NT = (1 << k) >> RB, NW = NT / 32;
     // one state in registers: a ring of db staging tiles and one re-layout
     // tile; otherwise a staging and a re-layout tile per state
     const bool one = S == 1 || seq;
     const size_t tiles = one ? (size_t)std::max(1, std::min(2, db)) + (pp ? 2 : 1) : (size_t)2 * S;
-    return tiles * 4096 * 8 + (size_t)n_events * S * NW * 8 * sizeof(double);
+    return tiles * ((size_t)8 << k) + (size_t)n_events * S * NW * 8 * sizeof(double);
 }
 
 cudaError_t jit_launch(const JitPass& p, int grid, const PassArgs& a, cudaStream_t st) {
@@ -1272,7 +1280,7 @@ cudaError_t jit_launch(const JitPass& p, int grid, const PassArgs& a, cudaStream
     j.err = a.err;
     j.n_tiles = a.n_tiles;
     void* args[] = {&j};
-    return cudaLaunchKernel((const void*)p.kernel, dim3(grid), dim3(4096 >> p.RB), args, p.smem_bytes(), st);
+    return cudaLaunchKernel((const void*)p.kernel, dim3(grid), dim3((1 << p.k) >> p.RB), args, p.smem_bytes(), st);
 }
 
 }  // namespace nqs

@@ -13,12 +13,13 @@ namespace nqs {
 // Everything the generator needs from one register-resident launch.
 struct JitPass {
     int S = 1, RB = 4, n = 0;
+    int k = kMaxTileQ;        // tile qubits (12, or 13 with 512-thread blocks)
     bool pp = false;          // one-state kernels: two re-layout buffers, one barrier per re-layout
     int hint = 0;             // L2 policies: 1 state tiles evict-first, 2 phi kept for the other states
     int rv = 1;               // site reduction form: 1 conj-multiply-add, 2 split accumulators
     int db = 1;               // staging buffers of one-state kernels (1 or 2)
     bool seq = false;         // multi-state pass swept one state at a time (2 blocks per SM)
-    int local[kMaxTileQ] = {};
+    int local[kTileSlots] = {};
     int nonlocal[kMaxQ] = {};
     int n_events = 0;
     int err_timeout = NQS_ERR_DEVICE_TIMEOUT;

@@ -11,6 +11,8 @@
 namespace nqs {
 
 constexpr int kMaxTileQ = 12;          // 4096 amplitudes = 32 KB per state tile
+constexpr int kWideTileQ = 13;         // generated kernels: 8192 amplitudes, 512-thread blocks
+constexpr int kTileSlots = 13;         // tile-qubit slots of the pass records
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxEvents = 8;          // reductions per pass (the planner cuts passes accordingly)
@@ -73,7 +75,7 @@ struct PassArgs {
     const float2* mats;
     int n, k, c;
     int n_events;
-    int local[kMaxTileQ];
+    int local[kTileSlots];
     int nonlocal[kMaxQ];
     long long n_tiles;
     const float2* in[3];
