@@ -185,6 +185,16 @@ int nqs_term_values(nqs_handle h, double* out, size_t cap, size_t* count);
  * dropped and dominant parts, Theorem 1's argument per site). */
 int nqs_truncation_bound(nqs_handle h, int level, double* out);
 
+/* Check of the sweep plan (host only, test hook): the largest entry
+ * difference between the operator of the plan's operation order (fused
+ * gates, the Hadamard-diagonal rewrite, the reordering before segmentation,
+ * K_0 at the noise sites) and the operator of the circuit itself with K_0
+ * after each noise's gate, both applied to every basis state in FP64.  No
+ * counterpart in the paper (the plan is this library's).  n <= 10.
+ * Errors: NQS_ERR_ARG, NQS_ERR_ORDER (not prepared), NQS_ERR_UNSUPPORTED
+ * (general noises), NQS_ERR_TOO_LARGE (n > 10). */
+int nqs_plan_check(nqs_handle h, double* max_abs_err);
+
 /* The kept terms (canonical order, level `level`) that shard `rank` of
  * `count` evaluates under NQS_OPT_SHARD_RANK / NQS_OPT_SHARD_COUNT: mask[i]
  * = 1 for its terms; *n receives the term count (call with mask = NULL or

@@ -318,6 +318,16 @@ int nqs_term_values(nqs_handle hh, double* out, size_t cap, size_t* count) {
     return engine_term_values(*h, out, cap, count);
 }
 
+int nqs_plan_check(nqs_handle hh, double* max_abs_err) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !max_abs_err) return NQS_ERR_ARG;
+    if (!h->prepared) return NQS_ERR_ORDER;
+    if (h->general) return NQS_ERR_UNSUPPORTED;
+    if (h->circ.n > 10) return NQS_ERR_TOO_LARGE;
+    *max_abs_err = plan_product_error(h->circ, h->factors, h->plan);
+    return NQS_OK;
+}
+
 int nqs_truncation_bound(nqs_handle hh, int level, double* out) {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h || !out || level < 0) return NQS_ERR_ARG;

@@ -350,4 +350,66 @@ std::vector<PassSpec> segment(const Plan& p, bool cut_after_sites, int max_sites
     return out;
 }
 
+// Largest entry difference between the operator of the plan's operation order
+// and that of the circuit with K_0 at every noise site (both applied to every
+// basis state, FP64): fusion, the Hadamard rewrite and the reordering must
+// leave the product unchanged.
+double plan_product_error(const Circuit& c, const std::vector<Factors>& f, const Plan& p) {
+    const int n = c.n;
+    const size_t D = (size_t)1 << n;
+    auto apply1 = [&](std::vector<cd>& v, int q, const cd* m) {
+        const size_t b = (size_t)1 << q;
+        for (size_t i = 0; i < D; ++i)
+            if (!(i & b)) {
+                const cd x0 = v[i], x1 = v[i | b];
+                v[i] = m[0] * x0 + m[1] * x1;
+                v[i | b] = m[2] * x0 + m[3] * x1;
+            }
+    };
+    auto apply2 = [&](std::vector<cd>& v, int q0, int q1, const cd* m) {   // row 2*b(q0) + b(q1)
+        const size_t b0 = (size_t)1 << q0, b1 = (size_t)1 << q1;
+        for (size_t i = 0; i < D; ++i)
+            if (!(i & b0) && !(i & b1)) {
+                const size_t idx[4] = {i, i | b1, i | b0, i | b0 | b1};
+                cd x[4], y[4];
+                for (int e = 0; e < 4; ++e) x[e] = v[idx[e]];
+                for (int r = 0; r < 4; ++r) {
+                    y[r] = 0.0;
+                    for (int e = 0; e < 4; ++e) y[r] += m[4 * r + e] * x[e];
+                }
+                for (int e = 0; e < 4; ++e) v[idx[e]] = y[e];
+            }
+    };
+    double err = 0.0;
+    std::vector<cd> a(D), b(D);
+    for (size_t col = 0; col < D; ++col) {
+        std::fill(a.begin(), a.end(), cd(0.0));
+        std::fill(b.begin(), b.end(), cd(0.0));
+        a[col] = b[col] = 1.0;
+        size_t ns = 0;
+        auto sites = [&](int g) {
+            for (; ns < c.noises.size() && c.noises[ns].after_gate == g; ++ns)
+                apply1(a, c.noises[ns].qubit, f[ns].K[0].data());
+        };
+        sites(-1);
+        for (size_t g = 0; g < c.gates.size(); ++g) {
+            const Gate& gt = c.gates[g];
+            if (gate_is_two_qubit(gt.kind)) {
+                const Mat4 m = gate_matrix_2q(gt);
+                apply2(a, gt.q0, gt.q1, m.data());
+            } else {
+                const Mat2 m = gate_matrix_1q(gt);
+                apply1(a, gt.q0, m.data());
+            }
+            sites((int)g);
+        }
+        for (const HostOp& o : p.ops) {
+            if (o.type == OP_G2 || o.type == OP_D2) apply2(b, o.q0, o.q1, o.m.data());
+            else apply1(b, o.q0, o.m.data());
+        }
+        for (size_t i = 0; i < D; ++i) err = std::max(err, std::abs(a[i] - b[i]));
+    }
+    return err;
+}
+
 }  // namespace nqs

@@ -112,6 +112,9 @@ void build_plan(const Circuit& c, const std::vector<Factors>& f, int tile_qubits
 // max_ops_per_pass operations.
 std::vector<PassSpec> segment(const Plan& p, bool cut_after_sites, int max_sites_per_pass, int max_ops_per_pass,
                               const std::vector<char>* cut_after = nullptr);
+// Largest entry difference between the plan's operator product and the
+// circuit's (gates, K_0 at the noise sites), on every basis state (n <= 10).
+double plan_product_error(const Circuit& c, const std::vector<Factors>& f, const Plan& p);
 
 // ------------------------------------------ general noises (generic.cu)
 // Factors of a one- or two-qubit noise given by Kraus operators or by its

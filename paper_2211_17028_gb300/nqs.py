@@ -118,6 +118,7 @@ _SIGS = {
     "nqs_term_values": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t,
                                        ctypes.POINTER(ctypes.c_size_t)]),
     "nqs_truncation_bound": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "nqs_plan_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "nqs_shard_mask": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "nqs_general_factors": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32),
@@ -349,6 +350,14 @@ def nqs_term_values(h):
     _check(_lib().nqs_term_values(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cnt.value,
                                   ctypes.byref(cnt)), "nqs_term_values")
     return out[:cnt.value]
+
+
+def nqs_plan_check(h):
+    """Largest entry difference between the plan's operator product and the
+    circuit's (host only, n <= 10)."""
+    out = ctypes.c_double()
+    _check(_lib().nqs_plan_check(h, ctypes.byref(out)), "nqs_plan_check")
+    return out.value
 
 
 def nqs_truncation_bound(h, level):

@@ -161,6 +161,32 @@ def test_plan_shapes():
     nqs.nqs_destroy(h)
 
 
+@pytest.mark.parametrize("make", [
+    lambda: W.c1_line6(),
+    lambda: W.qaoa_workload(8, 3, 6, 3, "ideal", "qaoa8"),
+    lambda: W.qaoa_workload(10, 5, 8, 2, "ideal", "qaoa10"),
+    lambda: W.random_circuit(51, 7, 60, 6, noise_kinds=("ad", "pd", "adpd", "depol"), v_kind="ideal"),
+    lambda: W.random_circuit(52, 9, 90, 8, v_kind="ideal"),
+], ids=["line6", "qaoa8", "qaoa10", "random7", "random9"])
+def test_plan_operator_equals_circuit_operator(make):
+    # fusion, the Hadamard-diagonal rewrite and the reordering before
+    # segmentation keep the product of the operations (K_0 at the sites)
+    h = _handle(make())
+    assert nqs.nqs_plan_check(h) <= 1e-12
+    nqs.nqs_destroy(h)
+
+
+def test_plan_reordering_cuts_passes():
+    # the 30-qubit QAOA workload: 20 passes per sweep in circuit order, 15 after
+    # hoisting commuting operations into earlier passes
+    h = _handle(W.c3_qaoa30())
+    assert nqs.nqs_get_info(h)["n_passes"] <= 15
+    with pytest.raises(nqs.NqsError) as e:
+        nqs.nqs_plan_check(h)
+    assert e.value.code == nqs.NQS_ERR_TOO_LARGE
+    nqs.nqs_destroy(h)
+
+
 def test_prune_flag_drops_zero_rank_factors():
     # amplitude damping has Kraus rank 2: with pruning only factor 1 remains
     h = nqs.nqs_load_circuit("nqs-ir 1\nqubits 2\ngate h 0\ngate cx 0 1\n")
