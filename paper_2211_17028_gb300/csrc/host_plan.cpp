@@ -18,6 +18,7 @@
 // applies.  Diagonal operations on qubits outside the tile read the qubit's
 // value from the tile's base index.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 
 #include "nqs_internal.h"
@@ -278,7 +279,10 @@ void build_plan(const Circuit& c, const std::vector<Factors>& f, int tile_qubits
                 for (int cc = 0; cc < 4; ++cc)
                     if (r != cc) o.m[4 * r + cc] = cd(0);
     }
-    lookahead_order(p, 4, 96);
+    {
+        const char* e = std::getenv("NQS_PLAN_REORDER");   // 0: keep the circuit order
+        if (!(e && e[0] == '0')) lookahead_order(p, 4, 96);
+    }
     // bounded passes: at most 4 reductions and 96 operations each, so a pass's
     // program and reduction slots fit next to the tiles in shared memory
     p.free_passes = segment(p, false, 4, 96);
