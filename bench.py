@@ -76,6 +76,8 @@ def parse_args():
                          "level sums (strong scaling) instead of one replica per rank")
     ap.add_argument("--rb", type=int, default=0, choices=[0, 3, 4],
                     help="register qubits of multi-state sweep passes (NQS_OPT_SWEEP_RB; 0 automatic)")
+    ap.add_argument("--coverage", type=int, default=10,
+                    help="twin20_is: independent 2000-draw learned estimates whose |error| / stderr is reported")
     ap.add_argument("--launch-list", default=None,
                     help="write the timed schedule's launch list (nqs_schedule_launches) to this JSON file")
     return ap.parse_args()
@@ -619,7 +621,7 @@ def run_twin_is(args):
     full, t_full = timed(lambda: circ.fidelity(psi, v, 3))
     F3, T3 = full["F"], full["T"][3]
 
-    def sampled(use_net):
+    def sampled(use_net, keep=None):
         t0 = time.perf_counter()
         r2 = circ.fidelity(psi, v, 2)
         vals = circ.term_values()
@@ -649,14 +651,30 @@ def run_twin_is(args):
             draws *= 2
             seed += 1
         t_total = time.perf_counter() - t0
-        if m is not None:
+        if keep is not None:
+            keep.update(m=m, feats=feats, W1=W1, alpha=alpha)
+        elif m is not None:
             nqs.nqs_mlp_destroy(m)
         F_est = r2["F"] + est["estimate"]
         return {"s": t_total, "setup_s": t_setup, "draws": draws, "rounds": rounds, "T3": est["estimate"],
                 "stderr": est["stderr_"], "three_sigma_within_target": 3.0 * est["stderr_"] <= target,
                 "abs_dF_vs_level3": abs(F_est - F3), "reached": abs(F_est - F3) <= target}
 
-    learned = sampled(True)
+    net = {}
+    learned = sampled(True, net)
+    # calibration of the reported standard error: independent estimates with
+    # the trained network, each against the exact T_3 of the enumeration
+    cover = None
+    if args.coverage > 0:
+        z = []
+        for j in range(args.coverage):
+            e = nqs.nqs_is_estimate(circ.h, net["m"], 3, 2000, net["alpha"], 5000 + j, net["feats"], net["W1"])
+            z.append((e["estimate"] - T3) / e["stderr_"])
+        z = np.abs(np.array(z))
+        cover = {"estimates": args.coverage, "draws_each": 2000, "within_1_sigma": float(np.mean(z <= 1)),
+                 "within_2_sigma": float(np.mean(z <= 2)), "within_3_sigma": float(np.mean(z <= 3)),
+                 "max_abs_z": float(z.max())}
+    nqs.nqs_mlp_destroy(net["m"])
     uniform = sampled(False)
     clk = clocks.stop()
     n3 = math.comb(N, 3) * 27
@@ -668,7 +686,7 @@ def run_twin_is(args):
                        "noises": N, "rates": "log-uniform [1e-3, 5e-3]", "alpha": 0.3, "level3_terms": n3,
                        "l2": "L2-resident states (8 MiB)"},
             "plain_level3": {"s": t_full, "F": F3, "T3": T3, "terms": full["n_terms"]},
-            "learned": learned, "uniform": uniform,
+            "learned": learned, "uniform": uniform, "coverage": cover,
             "time_to_dF_1e-6": {"plain_s": t_full, "learned_s": learned["s"] if learned["reached"] else None,
                                 "uniform_s": uniform["s"] if uniform["reached"] else None},
             "clocks": clk}
