@@ -10,6 +10,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -49,7 +50,8 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 template <typename TB, bool TA_T, bool TB_T>
 __global__ void __launch_bounds__(128) gemm_kernel(int M, int N, int K, const float* __restrict__ A,
                                                    const TB* __restrict__ B, float* __restrict__ C,
-                                                   const float* __restrict__ bias, int relu, int accumulate) {
+                                                   const float* __restrict__ bias, int relu, int accumulate,
+                                                   int kchunk, float* __restrict__ part) {
     constexpr bool kSplitB = !std::is_same<TB, __nv_bfloat16>::value;
     // tiles: A as [m][k], B as [n][k] (k contiguous: one 32-bit word holds the k, k+1 pair)
     __shared__ __nv_bfloat16 Ah[kBM][kBK + kPad], Al[kBM][kBK + kPad];
@@ -65,11 +67,14 @@ __global__ void __launch_bounds__(128) gemm_kernel(int M, int N, int K, const fl
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-    for (int k0 = 0; k0 < K; k0 += kBK) {
+    // split K: block z covers [z * kchunk, (z + 1) * kchunk) and writes its
+    // partial product to part[z] (summed in a fixed order by splitk_sum_kernel)
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    for (int k0 = kb; k0 < ke; k0 += kBK) {
         for (int e = tid; e < kBM * kBK; e += blockDim.x) {
             const int r = e / kBK, k = e % kBK, m = m0 + r, kk = k0 + k;
             float a = 0.f;
-            if (m < M && kk < K) a = TA_T ? A[(size_t)kk * M + m] : A[(size_t)m * K + kk];
+            if (m < M && kk < ke) a = TA_T ? A[(size_t)kk * M + m] : A[(size_t)m * K + kk];
             const __nv_bfloat16 hi = __float2bfloat16(a);
             Ah[r][k] = hi;
             Al[r][k] = __float2bfloat16(a - __bfloat162float(hi));
@@ -77,7 +82,7 @@ __global__ void __launch_bounds__(128) gemm_kernel(int M, int N, int K, const fl
         for (int e = tid; e < kBN * kBK; e += blockDim.x) {
             const int c = e / kBK, k = e % kBK, n = n0 + c, kk = k0 + k;
             float b = 0.f;
-            if (n < N && kk < K) {
+            if (n < N && kk < ke) {
                 if constexpr (TB_T) b = (float)B[(size_t)n * K + kk];
                 else b = (float)B[(size_t)kk * N + n];
             }
@@ -129,6 +134,10 @@ __global__ void __launch_bounds__(128) gemm_kernel(int M, int N, int K, const fl
                 const int n = n0 + wn + 8 * j + 2 * t + (e & 1);
                 if (m >= M || n >= N) continue;
                 float v = acc[i][j][e];
+                if (part) {
+                    part[((size_t)blockIdx.z * M + m) * N + n] = v;
+                    continue;
+                }
                 if (bias) v += bias[n];
                 if (relu) v = fmaxf(v, 0.f);
                 float* dst = C + (size_t)m * N + n;
@@ -136,11 +145,33 @@ __global__ void __launch_bounds__(128) gemm_kernel(int M, int N, int K, const fl
             }
 }
 
+// C (+)= sum over z of part[z] (fixed order), for split-K products
+__global__ void splitk_sum_kernel(const float* __restrict__ part, int splits, size_t mn, float* __restrict__ C,
+                                  int accumulate) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < mn; i += (size_t)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        for (int z = 0; z < splits; ++z) v += part[(size_t)z * mn + i];
+        C[i] = accumulate ? C[i] + v : v;
+    }
+}
+
+// ksplit > 1 (no bias or ReLU): K is cut into ksplit chunks computed by
+// separate blocks into `part` (ksplit * M * N floats) and summed afterwards
 template <typename TB, bool TA_T, bool TB_T>
 void gemm(int M, int N, int K, const float* A, const TB* B, float* C, const float* bias, bool relu, bool accumulate,
-          cudaStream_t st) {
-    dim3 block(128), grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM);
-    gemm_kernel<TB, TA_T, TB_T><<<grid, block, 0, st>>>(M, N, K, A, B, C, bias, relu ? 1 : 0, accumulate ? 1 : 0);
+          cudaStream_t st, int ksplit = 1, float* part = nullptr) {
+    if (ksplit < 1 || !part || bias || relu) ksplit = 1;
+    int kchunk = (K + ksplit - 1) / ksplit;
+    kchunk = (kchunk + kBK - 1) / kBK * kBK;
+    ksplit = (K + kchunk - 1) / kchunk;
+    dim3 block(128), grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM, ksplit);
+    gemm_kernel<TB, TA_T, TB_T><<<grid, block, 0, st>>>(M, N, K, A, B, C, bias, relu ? 1 : 0, accumulate ? 1 : 0,
+                                                         kchunk, ksplit > 1 ? part : nullptr);
+    if (ksplit > 1) {
+        const size_t mn = (size_t)M * N;
+        const int blocks = (int)std::min<size_t>(1024, (mn + 255) / 256);
+        splitk_sum_kernel<<<blocks, 256, 0, st>>>(part, ksplit, mn, C, accumulate ? 1 : 0);
+    }
 }
 
 __global__ void to_bf16_kernel(const float* __restrict__ w, __nv_bfloat16* __restrict__ wb, int n) {
@@ -153,13 +184,23 @@ __global__ void relu_back_kernel(float* __restrict__ d, const float* __restrict_
         if (y[i] <= 0.f) d[i] = 0.f;
 }
 
-// column sums (bias gradients): db[n] += sum_m dY[m][n]
+// column sums (bias gradients): db[n] += sum_m dY[m][n]; a block of 32 x 8
+// threads covers 32 columns, each thread a strided eighth of the rows, then
+// the eight partial sums are added in a fixed order
 __global__ void colsum_kernel(const float* __restrict__ d, float* __restrict__ db, int M, int N) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+    __shared__ float part[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int n = blockIdx.x * 32 + tx;
     float s = 0.f;
-    for (int m = 0; m < M; ++m) s += d[(size_t)m * N + n];
-    db[n] += s;
+    if (n < N)
+        for (int m = ty; m < M; m += 8) s += d[(size_t)m * N + n];
+    part[ty][tx] = s;
+    __syncthreads();
+    if (ty == 0 && n < N) {
+        float t = 0.f;
+        for (int r = 0; r < 8; ++r) t += part[r][tx];
+        db[n] += t;
+    }
 }
 
 // MSE: loss partials and dY = 2 (pred - y) / B
@@ -231,6 +272,8 @@ struct Mlp {
     double* loss_dev = nullptr;
     float* Xb = nullptr;
     float* yb = nullptr;
+    int ksplit = 1;               // K splits of the weight-gradient products
+    float* part = nullptr;        // their partial products
     std::vector<void*> blocks;
     std::vector<size_t> block_bytes;
 };
@@ -266,6 +309,16 @@ int ensure_batch(Mlp& M, int B) {
     M.Xb = (float*)dev_alloc((size_t)B * M.dims[0] * sizeof(float), nullptr);
     M.yb = (float*)dev_alloc((size_t)B * sizeof(float), nullptr);
     if (!M.Xb || !M.yb) return NQS_ERR_NOMEM;
+    // weight-gradient products: about 256 blocks of 64 x 64 outputs in all
+    size_t wmax = 0, tiles = 1;
+    for (size_t l = 0; l + 1 < M.dims.size(); ++l) {
+        wmax = std::max(wmax, (size_t)M.dims[l] * M.dims[l + 1]);
+        tiles = std::max(tiles, (size_t)((M.dims[l] + 63) / 64) * ((M.dims[l + 1] + 63) / 64));
+    }
+    M.ksplit = (int)std::max<size_t>(1, std::min<size_t>((size_t)(B + kBK - 1) / kBK, 256 / tiles));
+    dev_free(M.part, 0, nullptr);
+    M.part = M.ksplit > 1 ? (float*)dev_alloc((size_t)M.ksplit * wmax * sizeof(float), nullptr) : nullptr;
+    if (M.ksplit > 1 && !M.part) return NQS_ERR_NOMEM;
     M.cap_B = B;
     return NQS_OK;
 }
@@ -293,8 +346,9 @@ int backward(Mlp& M, const float* X, const float* y, int B, cudaStream_t st) {
         if (l + 1 < L) relu_back_kernel<<<256, 256, 0, st>>>(dY, M.acts[l + 1], B * N);
         const float* Xin = (l == 0) ? X : M.acts[l];
         // dW[N x K] = dY^T [N x B] * X [B x K]
-        gemm<float, true, false>(N, K, B, dY, Xin, M.g + M.w_off[l], nullptr, false, true, st);
-        colsum_kernel<<<(N + 255) / 256, 256, 0, st>>>(dY, M.g + M.b_off[l], B, N);
+        // (the batch is the long dimension: split it so the product fills the GPU)
+        gemm<float, true, false>(N, K, B, dY, Xin, M.g + M.w_off[l], nullptr, false, true, st, M.ksplit, M.part);
+        colsum_kernel<<<(N + 31) / 32, 256, 0, st>>>(dY, M.g + M.b_off[l], B, N);
         // dX[B x K] = dY [B x N] * W [N x K]
         if (l > 0) gemm<__nv_bfloat16, false, false>(B, K, N, dY, M.wb + M.w_off[l], M.dacts[l], nullptr, false, false, st);
     }
@@ -317,6 +371,7 @@ void mlp_destroy(Mlp* M) {
     }
     dev_free(M->Xb, 0, nullptr);
     dev_free(M->yb, 0, nullptr);
+    dev_free(M->part, 0, nullptr);
     delete M;
 }
 
