@@ -593,8 +593,8 @@ def run_twin_is(args):
     whose truncation reaches |dF| <= 1e-6 (its level-4 remainder is far
     below).  Learned path: level 2, site features and pair targets from its
     term values, network training on the GPU, site-set checkpoints, then
-    importance-sampled T_3 in rounds of doubling size until three standard
-    errors are within 1e-6.  The same with the uniform proposal (the method
+    importance-sampled T_3 in rounds of independent draws pooled into one
+    estimate, the total doubling until three standard errors are within 1e-6.  The same with the uniform proposal (the method
     without the network).  Both are judged by |dF| against the level-3 F."""
     import numpy as np
     import torch
@@ -642,14 +642,24 @@ def run_twin_is(args):
         torch.cuda.synchronize()
         t_setup = time.perf_counter() - t0
         alpha = 0.3 if use_net else 1.0
-        draws, est, seed, rounds = 500, None, 99, []
+        # rounds of independent draws (a new seed each) pooled into one mean:
+        # the pooled standard error is sqrt(sum n_i^2 se_i^2) / sum n_i; the
+        # next round doubles the total until three standard errors are within
+        # the target
+        size, seed, rounds = 500, 99, []
+        tot, wsum, vsum = 0, 0.0, 0.0
         while True:
-            est = nqs.nqs_is_estimate(circ.h, m, 3, draws, alpha, seed, feats, W1)
-            rounds.append(draws)
-            if 3.0 * est["stderr_"] <= target or draws >= 64000:
+            e = nqs.nqs_is_estimate(circ.h, m, 3, size, alpha, seed, feats, W1)
+            rounds.append(size)
+            tot += size
+            wsum += size * e["estimate"]
+            vsum += (size * e["stderr_"]) ** 2
+            est = {"estimate": wsum / tot, "stderr_": math.sqrt(vsum) / tot}
+            if 3.0 * est["stderr_"] <= target or tot >= 64000:
                 break
-            draws *= 2
+            size = tot
             seed += 1
+        draws = tot
         t_total = time.perf_counter() - t0
         if keep is not None:
             keep.update(m=m, feats=feats, W1=W1, alpha=alpha)
