@@ -620,6 +620,9 @@ def run_twin_is(args):
     clocks.start()
     full, t_full = timed(lambda: circ.fidelity(psi, v, 3))
     F3, T3 = full["F"], full["T"][3]
+    # exact per-set weights W(S) of the enumeration (27 factor tuples per set)
+    o3 = 1 + 3 * N + 9 * (N * (N - 1) // 2)
+    W3 = circ.term_values()[o3:].reshape(-1, 27).sum(1)
 
     def sampled(use_net, keep=None):
         t0 = time.perf_counter()
@@ -661,12 +664,25 @@ def run_twin_is(args):
             seed += 1
         draws = tot
         t_total = time.perf_counter() - t0
+        # the estimator's exact variance per draw from the enumeration's W(S)
+        # and the proposal's probabilities q(S): sum W^2 / q - T_3^2; the draws
+        # three standard errors need to be within the target, and the time
+        # they take at this run's rate per draw
+        q = nqs.nqs_is_proposal(circ.h, m, 3, alpha, feats, W1)
+        pos = q > 0
+        second = float(np.sum(W3[pos] ** 2 / q[pos])) if np.all(W3[~pos] == 0) else float("inf")
+        var1 = max(second - T3 * T3, 0.0)
+        need = int(math.ceil(9.0 * var1 / (target * target)))
+        per_draw = (t_total - t_setup) / draws
+        expected_s = t_setup + need * per_draw
         if keep is not None:
             keep.update(m=m, feats=feats, W1=W1, alpha=alpha)
         elif m is not None:
             nqs.nqs_mlp_destroy(m)
         F_est = r2["F"] + est["estimate"]
         return {"s": t_total, "setup_s": t_setup, "draws": draws, "rounds": rounds, "T3": est["estimate"],
+                "exact_rel_var_per_draw": var1 / (T3 * T3), "draws_for_3sigma": need, "s_per_draw": per_draw,
+                "expected_s_to_target": expected_s,
                 "stderr": est["stderr_"], "three_sigma_within_target": 3.0 * est["stderr_"] <= target,
                 "abs_dF_vs_level3": abs(F_est - F3), "reached": abs(F_est - F3) <= target}
 
@@ -688,17 +704,25 @@ def run_twin_is(args):
     uniform = sampled(False)
     clk = clocks.stop()
     n3 = math.comb(N, 3) * 27
-    line = {"metric": METRIC, "value": (t_full / learned["s"]) if learned["reached"] else None,
-            "unit": "time-to-|dF|<=1e-6 speedup over the plain level-3 expansion", "n_gpus": 1, "steps": 1,
-            "warmup": 0, "ms_per_step": 1000.0 * learned["s"], "higher_is_better": True, "scaling": "weak",
+    # headline: the expected time until three exact standard errors are within
+    # the target (set-up + the draws that needs at the measured rate), which a
+    # sampled standard error of these heavy-tailed weights cannot judge reliably;
+    # the sampled runs are reported beside it
+    line = {"metric": METRIC, "value": t_full / learned["expected_s_to_target"],
+            "unit": "time-to-|dF|<=1e-6 speedup over the plain level-3 expansion (expected, 3 exact standard errors)",
+            "n_gpus": 1, "steps": 1,
+            "warmup": 0, "ms_per_step": 1000.0 * learned["expected_s_to_target"], "higher_is_better": True,
+            "scaling": "weak",
             "vs_baseline": None, "dtype": "c64 sweeps, bf16/fp32 network", "data": "synthetic",
             "config": {"workload": "twin20_is", "description": WORKLOADS["twin20_is"][2], "n_qubits": w.n,
                        "noises": N, "rates": "log-uniform [1e-3, 5e-3]", "alpha": 0.3, "level3_terms": n3,
                        "l2": "L2-resident states (8 MiB)"},
             "plain_level3": {"s": t_full, "F": F3, "T3": T3, "terms": full["n_terms"]},
             "learned": learned, "uniform": uniform, "coverage": cover,
-            "time_to_dF_1e-6": {"plain_s": t_full, "learned_s": learned["s"] if learned["reached"] else None,
-                                "uniform_s": uniform["s"] if uniform["reached"] else None},
+            "time_to_dF_1e-6": {"plain_s": t_full, "learned_expected_s": learned["expected_s_to_target"],
+                                "uniform_expected_s": uniform["expected_s_to_target"],
+                                "learned_sampled_s": learned["s"] if learned["reached"] else None,
+                                "uniform_sampled_s": uniform["s"] if uniform["reached"] else None},
             "clocks": clk}
     print(json.dumps(line))
     circ.close()
