@@ -21,6 +21,11 @@ Printed JSON keys beyond the basic contract:
   e2e           -- the same metric through the public C ABI from host data:
                    circuit text parsed, noise factored, schedule uploaded,
                    result read back to pageable host memory, every step.
+  time_to_dF    -- time to |dF| <= 1e-6 against the plain GPU path: the
+                   512-circuit batch (batched vs one call per circuit) and
+                   the learned proposal on the hot-rate 200-noise twin
+                   (expected time from the exact variance per draw vs the
+                   plain level-3 enumeration).
 --impl reference times O3 alone, on the same config (the reference arm).
 """
 
@@ -450,6 +455,19 @@ def run_nqs(args):
             ttd = {"batch512": time_to_df_batch()}
         except Exception as ex:  # never sink the main measurement
             ttd = {"batch512": {"failed": str(ex)}}
+        # the learned proposal on the hot twin (plain level-3 enumeration as the time to beat)
+        try:
+            a2 = argparse.Namespace(**vars(args))
+            a2.coverage = 0
+            tw = run_twin_is(a2, emit=False)
+            ttd["twin20_is"] = {"workload": "twin20_is", "target_abs_dF": 1e-6,
+                                "speedup_expected": tw["value"], **tw["time_to_dF_1e-6"],
+                                "exact_rel_var_per_draw": {"learned": tw["learned"]["exact_rel_var_per_draw"],
+                                                           "uniform": tw["uniform"]["exact_rel_var_per_draw"]},
+                                "draws_for_3sigma": {"learned": tw["learned"]["draws_for_3sigma"],
+                                                     "uniform": tw["uniform"]["draws_for_3sigma"]}}
+        except Exception as ex:  # never sink the main measurement
+            ttd["twin20_is"] = {"failed": str(ex)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -584,7 +602,7 @@ def run_batch(args):
     return 0
 
 
-def run_twin_is(args):
+def run_twin_is(args, emit=True):
     """Learned proposal against the plain GPU expansion on the n=20 twin of
     the 200-noise grid circuit, rates from the upper part of the config's
     range ([1e-3, 5e-3]) so that the level-3 sum exceeds 1e-6.
@@ -724,7 +742,9 @@ def run_twin_is(args):
                                 "learned_sampled_s": learned["s"] if learned["reached"] else None,
                                 "uniform_sampled_s": uniform["s"] if uniform["reached"] else None},
             "clocks": clk}
-    print(json.dumps(line))
+    if emit:
+        print(json.dumps(line))
+    return line
     circ.close()
     return 0
 
