@@ -48,6 +48,7 @@ struct SetsState {
     float2* work_mat = nullptr;       // spaced: backward recomputation state
     float2** phi_bd_tab = nullptr;    // spaced: site -> phi boundary of its block
     std::vector<PassSpec> segs;       // spaced: passes cut after every block-last site
+    std::vector<PassSpec> fsegs;      // passes of the set sweeps: up to 16 sites each (K_0 only at most of them)
     std::vector<DevOp> mat_ops;       // spaced: backward ops saving phi at every site, per pass of segs
     std::vector<std::pair<int, int>> mat_pass;   // (first op in mat_ops, count) per pass, reversed order
     std::vector<int> mat_seg;         // segment index of each entry of mat_pass
@@ -109,9 +110,9 @@ std::vector<DevOp> emit_range(const Plan& plan, const SetsState& S, const PassSp
     return out;
 }
 
-int pass_of(const Plan& plan, int lin) {
-    for (size_t p = 0; p < plan.free_passes.size(); ++p)
-        if (plan.free_passes[p].op_begin <= lin && lin < plan.free_passes[p].op_end) return (int)p;
+int pass_of(const std::vector<PassSpec>& segs, int lin) {
+    for (size_t p = 0; p < segs.size(); ++p)
+        if (segs[p].op_begin <= lin && lin < segs[p].op_end) return (int)p;
     return -1;
 }
 
@@ -223,18 +224,31 @@ template <typename FlagFn, typename RankFn>
 void sweep_range(Prog& G, const Handle& h, const SetsState& S, int a, int b, FlagFn flag_of, int nstates,
                  float2* const* states, float2* const* spawn, int n_spawn, RankFn rank_of) {
     const Plan& plan = h.plan;
-    for (int p = pass_of(plan, a + 1); p >= 0 && p < (int)plan.free_passes.size(); ++p) {
-        const PassSpec& ps = plan.free_passes[p];
+    for (int p = pass_of(S.fsegs, a + 1); p >= 0 && p < (int)S.fsegs.size(); ++p) {
+        const PassSpec& ps = S.fsegs[p];
         const int lo = std::max(ps.op_begin, a + 1), hi = std::min(ps.op_end, b + 1);
         if (lo >= hi) break;
-        auto ops = emit_range(plan, S, ps, lo, hi, flag_of, h.factors);
         const bool has_last = hi == b + 1;
-        add_launch(G, plan, S, ps, nstates, ops, (const float2* const*)states, states, has_last ? spawn : nullptr,
-                   has_last ? n_spawn : 0);
-        std::vector<int> ev;
-        for (const DevOp& d : ops)
-            if (d.type == OP_SITE && (d.flags & FL_REDUCE)) ev.push_back(d.site);
-        if (!ev.empty()) add_finish_events(G, nstates, ev, h.factors, rank_of);
+        // one launch per run of at most four reductions (the kernels' reduction slots)
+        for (int c0 = lo; c0 < hi;) {
+            int c1 = c0, red = 0;
+            while (c1 < hi) {
+                const HostOp& o = plan.ops[c1];
+                const bool r = o.type == OP_SITE && (flag_of(o.site) & FL_REDUCE);
+                if (r && red == 4) break;
+                red += r;
+                ++c1;
+            }
+            auto ops = emit_range(plan, S, ps, c0, c1, flag_of, h.factors);
+            const bool last_chunk = has_last && c1 == hi;
+            add_launch(G, plan, S, ps, nstates, ops, (const float2* const*)states, states,
+                       last_chunk ? spawn : nullptr, last_chunk ? n_spawn : 0);
+            std::vector<int> ev;
+            for (const DevOp& d : ops)
+                if (d.type == OP_SITE && (d.flags & FL_REDUCE)) ev.push_back(d.site);
+            if (!ev.empty()) add_finish_events(G, nstates, ev, h.factors, rank_of);
+            c0 = c1;
+        }
         if (has_last) break;
     }
 }
@@ -372,6 +386,7 @@ int engine_prepare_sets(Handle& h, const nqs_state* psi, const nqs_state* v, voi
         S.segs = segment(plan, false, h.opt_max_sites > 0 ? h.opt_max_sites : 4,
                          h.opt_max_ops > 0 ? h.opt_max_ops : 96, &block_last);
     }
+    S.fsegs = segment(plan, false, 16, h.opt_max_ops > 0 ? h.opt_max_ops : 96);
     const std::vector<PassSpec>& bsegs = k ? S.segs : plan.free_passes;
     std::vector<DevOp> run_ops;
     Run run_bwd = make_run(plan, bsegs, RT_BWD, false, false, false, h.factors, S.tab, run_ops,
@@ -617,7 +632,7 @@ int engine_eval_sets(Handle& h, int k, const int* sets, size_t m, double* W_out,
         // spawn K_i chi_{s1} into the first group (shared by every set starting at s1)
         const int p1 = plan.site_pos[s1];
         const int m1 = h.factors[s1].m;
-        const PassSpec& ps1 = plan.free_passes[pass_of(plan, p1)];
+        const PassSpec& ps1 = S.fsegs[pass_of(S.fsegs, p1)];
         {
             auto ops = emit_range(plan, S, ps1, p1, p1 + 1, [&](int) { return FL_SPAWN; }, h.factors);
             const float2* in[1] = {chi_of(s1)};
