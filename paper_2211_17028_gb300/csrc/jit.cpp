@@ -13,14 +13,21 @@
 // depend on the thread or the tile stay run-time values.  Amplitudes whose
 // addresses are adjacent (the site's qubit or a register qubit being qubit 0)
 // move as 16-byte vectors.  The semantics are those of the interpreted
-// kernel: same tile (12 qubits), same TMA bulk prefetch with bounded mbarrier
-// waits, same phases and XOR-swizzled re-layouts, same site actions and the
-// same per-block FP64 partials, so the finishers and term sums are shared.
+// kernel: same tile (12 qubits; 13 with 512-thread blocks as an option), same
+// TMA bulk prefetch with bounded mbarrier waits, same phases and XOR-swizzled
+// re-layouts, same site actions and the same per-block FP64 partials, so the
+// finishers and term sums are shared.  The organisation differs: each kernel
+// holds one state of 16 amplitudes per thread, and a pass over the three (or
+// nine) states of a branch group sweeps a tile's states one after another
+// (twice the resident warps of holding them together; the tile's phi values
+// come from DRAM once and from L2 for the later states, under L2 eviction
+// policies), consecutive re-layouts alternate between two buffers, and site
+// reductions accumulate with split real/imaginary partners.
 //
 // Kernels are cached by their source text for the life of the process;
 // the distinct kernels of a schedule are compiled in parallel.  When NVRTC
 // cannot be loaded the engine keeps the interpreted kernel (still on the GPU)
-// and reports it through nqs_info.jit_kernels == 0.
+// and reports it through nqs_info.jit_state == -1 (jit_launches == 0).
 #include <cuda_runtime.h>
 #include <dlfcn.h>
 
@@ -269,8 +276,8 @@ struct Gen {
     std::set<int> early_phi;   // reductions of the current phase whose phi is loaded at the phase start
 
     // reductions per phase whose phi values may be held in registers from the
-    // phase start: the 16-amplitude layouts have the registers, the 8-amplitude
-    // three-state layout (128 registers per thread) does not
+    // phase start: only kernels holding several states in registers default to
+    // it (measured no gain for the one-state kernels)
     int early_phi_budget() const {
         if (const char* e = std::getenv("NQS_JIT_EARLY_PHI")) return std::atoi(e);
         return (RB >= 4 && S > 1) ? 2 : 0;
