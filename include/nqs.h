@@ -189,7 +189,8 @@ int nqs_truncation_bound(nqs_handle h, int level, double* out);
  * difference between the operator of the plan's operation order (fused
  * gates, the Hadamard-diagonal rewrite, the reordering before segmentation,
  * K_0 at the noise sites) and the operator of the circuit itself with K_0
- * after each noise's gate, both applied to every basis state in FP64.  No
+ * after each noise's gate, both applied to every basis state in FP64
+ * (+infinity when the plan does not keep the noise sites in their order).  No
  * counterpart in the paper (the plan is this library's).  n <= 10.
  * Errors: NQS_ERR_ARG, NQS_ERR_ORDER (not prepared), NQS_ERR_UNSUPPORTED
  * (general noises), NQS_ERR_TOO_LARGE (n > 10). */

@@ -325,6 +325,9 @@ int nqs_plan_check(nqs_handle hh, double* max_abs_err) {
     if (h->general) return NQS_ERR_UNSUPPORTED;
     if (h->circ.n > 10) return NQS_ERR_TOO_LARGE;
     *max_abs_err = plan_product_error(h->circ, h->factors, h->plan);
+    // the sweeps take the noise sites in their order: site_pos must increase
+    for (size_t s = 1; s < h->plan.site_pos.size(); ++s)
+        if (h->plan.site_pos[s] <= h->plan.site_pos[s - 1]) *max_abs_err = HUGE_VAL;
     return NQS_OK;
 }
 

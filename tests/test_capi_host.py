@@ -176,6 +176,17 @@ def test_plan_operator_equals_circuit_operator(make):
     nqs.nqs_destroy(h)
 
 
+@pytest.mark.parametrize("seed", range(60, 72))
+def test_plan_operator_random_circuits(seed):
+    # random widths, depths and noise placements, every gate kind of the reader
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(3, 9))
+    w = W.random_circuit(seed, n, int(rng.integers(10, 80)), int(rng.integers(1, 12)), v_kind="ideal")
+    h = _handle(w)
+    assert nqs.nqs_plan_check(h) <= 1e-12
+    nqs.nqs_destroy(h)
+
+
 def test_plan_reordering_cuts_passes():
     # the 30-qubit QAOA workload: 20 passes per sweep in circuit order, 15 after
     # hoisting commuting operations into earlier passes
