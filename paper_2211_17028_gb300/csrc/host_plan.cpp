@@ -78,58 +78,100 @@ std::array<cd, 16> matmul(const std::array<cd, 16>& a, const std::array<cd, 16>&
 
 bool op_is_diag(const HostOp& o) { return o.type == OP_D1 || o.type == OP_D2; }
 
+// One pass of the reordering over the remaining operations `rest` with the
+// tile qubits fixed to `tile`: every operation is taken (in order) when its
+// dense qubits are in the tile and it commutes with every operation skipped
+// before it in this pass -- two operations commute when they share no qubit or
+// are both diagonal; a noise site commutes with nothing on its qubit (the
+// branch states it spawns and the reduction it makes see the state at its
+// place) and sites keep their relative order.  Returns the count taken.
+int take_pass(const Plan& p, const std::vector<int>& rest, const std::vector<char>& tile, int max_sites, int max_ops,
+              std::vector<int>* taken, std::vector<int>* kept) {
+    std::vector<char> blk_diag(p.n, 0), blk_any(p.n, 0);
+    bool site_skipped = false;
+    int sites = 0, cnt = 0;
+    for (int idx : rest) {
+        const HostOp& o = p.ops[idx];
+        const int qs[2] = {o.q0, o.q1};
+        const int nq = o.q1 >= 0 ? 2 : 1;
+        const bool d = op_is_diag(o), site = o.type == OP_SITE;
+        bool ok = !(site && site_skipped) && cnt < max_ops && !(site && sites >= max_sites);
+        for (int j = 0; j < nq && ok; ++j)
+            if (blk_any[qs[j]] || (!d && blk_diag[qs[j]]) || (!d && !tile[qs[j]])) ok = false;
+        if (ok) {
+            sites += site;
+            ++cnt;
+            if (taken) taken->push_back(idx);
+        } else {
+            for (int j = 0; j < nq; ++j) (d ? blk_diag : blk_any)[qs[j]] = 1;
+            site_skipped = site_skipped || site;
+            if (kept) kept->push_back(idx);
+        }
+    }
+    return cnt;
+}
+
 // Reorders the operations so that in-order segmentation needs fewer passes.
-// Pass by pass, every remaining operation is taken (in order) when its dense
-// qubits still fit the tile and it commutes with every operation skipped before
-// it in this pass: two operations commute when they share no qubit or are both
-// diagonal.  A noise site commutes with nothing on its qubit (the branch states
-// it spawns and the reduction it makes see the state at its place), and sites
-// keep their relative order.  The reordered product of operations equals the
-// original one.
-void lookahead_order(Plan& p, int max_sites, int max_ops) {
+// Pass by pass: the tile holds the always-local low qubits and the dense
+// qubits of the first remaining operation, and is filled up to k qubits one
+// qubit at a time, each time with the qubit that lets the pass take the most
+// operations (take_pass); the pass then takes what it can.  The reordered
+// product of operations equals the original one (nqs_plan_check).  `passes`
+// receives the passes so formed (tile qubits ascending, padded to k with the
+// lowest unused qubits).
+void lookahead_order(Plan& p, int max_sites, int max_ops, std::vector<PassSpec>& passes) {
+    passes.clear();
     const int nops = (int)p.ops.size();
     std::vector<int> rest(nops), order;
     for (int i = 0; i < nops; ++i) rest[i] = i;
     order.reserve(nops);
     while (!rest.empty()) {
-        std::vector<char> in(p.n, 0), blk_diag(p.n, 0), blk_any(p.n, 0);
+        std::vector<char> tile(p.n, 0);
         int count = 0;
-        for (int q = 0; q < p.c; ++q) {
-            in[q] = 1;
-            ++count;
-        }
-        bool site_skipped = false;
-        int sites = 0, taken = 0;
-        std::vector<int> keep;
-        for (int idx : rest) {
-            const HostOp& o = p.ops[idx];
-            const int qs[2] = {o.q0, o.q1};
-            const int nq = o.q1 >= 0 ? 2 : 1;
-            const bool d = op_is_diag(o), site = o.type == OP_SITE;
-            bool ok = !(site && site_skipped) && taken < max_ops && !(site && sites >= max_sites);
-            for (int j = 0; j < nq && ok; ++j)
-                if (blk_any[qs[j]] || (!d && blk_diag[qs[j]])) ok = false;
-            int extra = 0;
-            if (!d)
-                for (int j = 0; j < nq; ++j)
-                    if (!in[qs[j]] && !(j == 1 && qs[1] == qs[0])) ++extra;
-            if (count + extra > p.k) ok = false;
-            if (ok) {
-                if (!d)
-                    for (int j = 0; j < nq; ++j)
-                        if (!in[qs[j]]) {
-                            in[qs[j]] = 1;
-                            ++count;
-                        }
-                sites += site;
-                ++taken;
-                order.push_back(idx);
-            } else {
-                for (int j = 0; j < nq; ++j) (d ? blk_diag : blk_any)[qs[j]] = 1;
-                site_skipped = site_skipped || site;
-                keep.push_back(idx);
+        auto add = [&](int q) {
+            if (q >= 0 && !tile[q]) {
+                tile[q] = 1;
+                ++count;
             }
+        };
+        for (int q = 0; q < p.c; ++q) add(q);
+        const HostOp& first = p.ops[rest[0]];
+        if (!op_is_diag(first)) {
+            add(first.q0);
+            add(first.q1);
         }
+        // candidates: dense qubits of the operations near the front
+        std::vector<char> cand(p.n, 0);
+        for (size_t i = 0; i < rest.size() && i < 512; ++i) {
+            const HostOp& o = p.ops[rest[i]];
+            if (op_is_diag(o)) continue;
+            cand[o.q0] = 1;
+            if (o.q1 >= 0) cand[o.q1] = 1;
+        }
+        while (count < p.k) {
+            int best = -1, best_v = -1;
+            for (int q = 0; q < p.n; ++q) {
+                if (tile[q] || !cand[q]) continue;
+                tile[q] = 1;
+                const int v = take_pass(p, rest, tile, max_sites, max_ops, nullptr, nullptr);
+                tile[q] = 0;
+                if (v > best_v) {
+                    best_v = v;
+                    best = q;
+                }
+            }
+            if (best < 0) break;
+            add(best);
+        }
+        std::vector<int> keep;
+        PassSpec ps;
+        ps.op_begin = (int)order.size();
+        take_pass(p, rest, tile, max_sites, max_ops, &order, &keep);
+        ps.op_end = (int)order.size();
+        for (int q = 0; q < p.n && count < p.k; ++q) add(q);
+        for (int q = 0; q < p.n; ++q)
+            if (tile[q]) ps.local.push_back(q);
+        passes.push_back(ps);
         rest.swap(keep);
     }
     std::vector<HostOp> ops;
@@ -279,13 +321,15 @@ void build_plan(const Circuit& c, const std::vector<Factors>& f, int tile_qubits
                 for (int cc = 0; cc < 4; ++cc)
                     if (r != cc) o.m[4 * r + cc] = cd(0);
     }
-    {
-        const char* e = std::getenv("NQS_PLAN_REORDER");   // 0: keep the circuit order
-        if (!(e && e[0] == '0')) lookahead_order(p, 4, 96);
-    }
     // bounded passes: at most 4 reductions and 96 operations each, so a pass's
     // program and reduction slots fit next to the tiles in shared memory
-    p.free_passes = segment(p, false, 4, 96);
+    {
+        const char* e = std::getenv("NQS_PLAN_REORDER");   // 0: keep the circuit order
+        if (!(e && e[0] == '0'))
+            lookahead_order(p, 4, 96, p.free_passes);
+        else
+            p.free_passes = segment(p, false, 4, 96);
+    }
     p.sitecut_passes = segment(p, true, 4, 96);
 }
 
