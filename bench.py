@@ -12,6 +12,9 @@ Printed JSON keys beyond the basic contract:
                    CUDA-event duration (events recorded by the library on the
                    launching stream during the timed steps), against the
                    measured HBM copy bandwidth;
+  roofline_fp32 -- the same launches' algorithmic FP32 flops over their time,
+                   against the FP32 FMA peak (the gate-heavy passes sit near
+                   the ridge between the two);
   cpu_baseline  -- the FP64 oracle O3 (forward/backward checkpoints, C/OpenMP)
                    on the host cores: the first state passes of its complete
                    call on this workload at full width, timed, scaled by the
@@ -94,6 +97,34 @@ def make_workload(name):
     if gen == "qaoa24":
         return W.qaoa_workload(24, 3, 20, 4, "ideal", "qaoa24"), level, desc
     return getattr(W, gen)(), level, desc
+
+
+# FP32 arithmetic peak of the GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) per clock
+FP32_LANES = 152 * 128
+
+
+def fp32_roofline(launches, stats, n, multi, sm_mhz):
+    """Algorithmic FP32 flops of the dominant sweep launches over their time,
+    against the FP32 FMA peak at the sampled SM clock.  Flops per amplitude of
+    every swept state: 16 per dense one-qubit gate (two complex multiply-adds),
+    32 per dense two-qubit gate, 6 per diagonal gate (one complex product), 16
+    per site reduction (the 2x2 reduced matrix), plus 16 per amplitude of every
+    spawned state; launches = the schedule of one call, stats = the kernel
+    statistics of the timed calls (launches, total_ms)."""
+    sel = [l for l in launches if l["kind"] == "pass" and ((l["states"] > 1) == multi)]
+    if not sel or not stats["total_ms"]:
+        return None
+    dim = float(2 ** n)
+    flops = 0.0
+    for l in sel:
+        per_amp = 16 * l["g1"] + 32 * l["g2"] + 6 * (l["d1"] + l["d2"]) + 16 * l["reductions"]
+        flops += dim * (l["states"] * per_amp + 16 * l["spawned"])
+    calls = stats["launches"] / len(sel)
+    achieved = flops * calls / (stats["total_ms"] / 1000.0) / 1e12
+    peak = FP32_LANES * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "flops_per_launch": flops / len(sel),
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x sampled SM clock (FMA peak)"}
 
 
 def measured_peaks():
@@ -422,9 +453,14 @@ def run_nqs(args):
     except Exception:
         pass
 
+    launch_list = nqs.nqs_schedule_launches(h)
     if args.launch_list and rank == 0:
         with open(args.launch_list, "w") as f:
-            json.dump(nqs.nqs_schedule_launches(h), f)
+            json.dump(launch_list, f)
+    try:   # the same launches against the FP32 arithmetic peak (near the ridge point)
+        roof_fp32 = fp32_roofline(launch_list, dom, w.n, dom is multi, clk.get("sm_mhz"))
+    except Exception as ex:  # never sink the main measurement
+        roof_fp32 = {"failed": str(ex)}
     # end to end through the public API from host data (the timed handle's
     # workspace is released first: the checkpoints of one call fill most of HBM)
     circ.close()
@@ -493,6 +529,7 @@ def run_nqs(args):
                          "share_of_step": dom["total_ms"] / (1000.0 * elapsed) if elapsed else None,
                          "all_sweeps_gbs": sweep["algorithmic_bytes"] / (sweep["total_ms"] / 1000.0) / 1e9
                          if sweep["total_ms"] else None},
+            "roofline_fp32": roof_fp32,
             "gpu_launches": int(sweep["launches"] + other["launches"] + fills["launches"]),
             "clocks": clk,
             "e2e": e2e,
