@@ -448,7 +448,8 @@ def run_nqs(args):
         with open(os.path.join(ROOT, "profiles", "sweep_traffic.json")) as f:
             tr = json.load(f)
         if (tr.get("workload") == args.workload and tr.get("kernel_source_sha") == kernel_source_sha(info["jit_launches"] > 0)
-                and tr.get("kernel") == ("multi" if dom is multi else "single")):
+                and tr.get("kernel") == ("multi" if dom is multi else "single")
+                and tr.get("plan_passes", info["n_passes"]) == info["n_passes"]):
             traffic = tr.get("dram_bytes_per_launch")
     except Exception:
         pass
