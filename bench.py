@@ -454,12 +454,17 @@ def run_nqs(args):
     except Exception:
         pass
 
-    launch_list = nqs.nqs_schedule_launches(h)
+    launch_list = None
+    try:
+        launch_list = nqs.nqs_schedule_launches(h)
+    except Exception:  # never sink the main measurement
+        if args.launch_list:
+            raise
     if args.launch_list and rank == 0:
         with open(args.launch_list, "w") as f:
             json.dump(launch_list, f)
     try:   # the same launches against the FP32 arithmetic peak (near the ridge point)
-        roof_fp32 = fp32_roofline(launch_list, dom, w.n, dom is multi, clk.get("sm_mhz"))
+        roof_fp32 = fp32_roofline(launch_list, dom, w.n, dom is multi, clk.get("sm_mhz")) if launch_list else None
     except Exception as ex:  # never sink the main measurement
         roof_fp32 = {"failed": str(ex)}
     # end to end through the public API from host data (the timed handle's
