@@ -12,7 +12,7 @@ counts and widths are beyond O2:
   the full enumeration's per-set sums W(S) on the heaviest and on random
   sets against O3's evaluation of those sets.
 Tolerances: 1e-5 relative on F, 1e-5 * F absolute on T_u, site-set sums and
-terms (the benchmark spec's tolerance); for the level-3 sets, whose W(S) are
+terms (the target tolerance); for the level-3 sets, whose W(S) are
 ~1e-12 of F, 1e-3 relative on sets with W(S) >= 1e-3 max W -- complex64
 amplitudes of magnitude |a| carry an absolute error of about 1e-7 * ||phi|| ||w||
 summed over ~700 operations, far below 1e-3 |a| for those sets.
