@@ -50,7 +50,8 @@ enum {
     NQS_ERR_ORDER = 7,          /* call sequence violated (e.g. fidelity before prepare) */
     NQS_ERR_DEVICE_TIMEOUT = 8, /* a bounded device-side wait gave up (reported in result.status) */
     NQS_ERR_UNSUPPORTED = 9,    /* request outside the supported range (documented per call) */
-    NQS_ERR_TOO_LARGE = 10      /* request exceeds a fixed capacity (nqs_reduced_matrix_noalloc) */
+    NQS_ERR_TOO_LARGE = 10,     /* request exceeds a fixed capacity (nqs_reduced_matrix_noalloc) */
+    NQS_ERR_COMPILE = 11        /* a generated kernel did not compile (nqs_jit_compile_check) */
 };
 
 typedef struct nqs_circuit* nqs_handle;
@@ -195,6 +196,17 @@ int nqs_truncation_bound(nqs_handle h, int level, double* out);
  * Errors: NQS_ERR_ARG, NQS_ERR_ORDER (not prepared), NQS_ERR_UNSUPPORTED
  * (general noises), NQS_ERR_TOO_LARGE (n > 10). */
 int nqs_plan_check(nqs_handle h, double* max_abs_err);
+
+/* Compile check of the pass-specialised kernels (host only, test hook; no
+ * counterpart in the paper): the kernels of the first `max_passes` passes of
+ * a forward sweep of the handle's plan over `states` states (1 or 3; with
+ * reductions at every site and, for one state, spawns) are generated with the
+ * library's current settings and compiled with NVRTC for sm_103a; nothing is
+ * loaded or run.  *compiled receives the number of kernels compiled.
+ * Errors: NQS_ERR_ARG, NQS_ERR_ORDER (not prepared), NQS_ERR_UNSUPPORTED
+ * (NVRTC not found, general noises, or fewer than 13 qubits: no generated
+ * kernels), NQS_ERR_COMPILE (a kernel failed; the message goes to stderr). */
+int nqs_jit_compile_check(nqs_handle h, int states, int max_passes, int* compiled);
 
 /* The kept terms (canonical order, level `level`) that shard `rank` of
  * `count` evaluates under NQS_OPT_SHARD_RANK / NQS_OPT_SHARD_COUNT: mask[i]

@@ -331,6 +331,14 @@ int nqs_plan_check(nqs_handle hh, double* max_abs_err) {
     return NQS_OK;
 }
 
+int nqs_jit_compile_check(nqs_handle hh, int states, int max_passes, int* compiled) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !compiled || (states != 1 && states != 3) || max_passes < 1) return NQS_ERR_ARG;
+    if (!h->prepared) return NQS_ERR_ORDER;
+    if (h->general) return NQS_ERR_UNSUPPORTED;
+    return engine_jit_compile_check(*h, states, max_passes, compiled);
+}
+
 int nqs_truncation_bound(nqs_handle hh, int level, double* out) {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h || !out || level < 0) return NQS_ERR_ARG;
@@ -739,6 +747,7 @@ const char* nqs_strerror(int code) {
         case NQS_ERR_DEVICE_TIMEOUT: return "a bounded device-side wait gave up";
         case NQS_ERR_UNSUPPORTED: return "request outside the supported range";
         case NQS_ERR_TOO_LARGE: return "request exceeds the fixed scratch capacity of the allocation-free entry point";
+        case NQS_ERR_COMPILE: return "a generated kernel did not compile";
         default: return "unknown status";
     }
 }

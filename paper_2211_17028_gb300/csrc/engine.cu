@@ -1275,6 +1275,51 @@ int engine_launch_list(const Handle& h, nqs_launch_info* out, size_t cap, size_t
     return NQS_OK;
 }
 
+int engine_jit_compile_check(Handle& h, int states, int max_passes, int* compiled) {
+    *compiled = 0;
+    const Plan& plan = h.plan;
+    if (plan.k != kMaxTileQ || !jit_available()) return NQS_ERR_UNSUPPORTED;
+    Tables tab;
+    std::vector<DevOp> dops;
+    std::vector<uint4> prog;
+    const Run run = make_run(plan, plan.free_passes, RT_FWD, true, states == 1, false, h.factors, tab, dops);
+    std::vector<std::unique_ptr<JitPass>> own;
+    std::vector<JitPass*> todo;
+    for (const RunPass& rp : run.passes) {
+        if ((int)todo.size() >= max_passes) break;
+        const ProgInfo pi = build_program(dops, rp.op_off, rp.n_ops, 4, tab, prog, plan.k);
+        std::unique_ptr<JitPass> jp(new JitPass());
+        jp->S = states;
+        jp->k = plan.k;
+        jp->RB = 4;
+        jp->n = plan.n;
+        jp->seq = states > 1 && jit_seq_enabled();
+        jp->db = jit_staging_buffers();
+        jp->pp = jit_pingpong();
+        jp->hint = jit_hint();
+        jp->rv = jit_reduction_form();
+        for (int j = 0; j < kTileSlots; ++j) jp->local[j] = rp.local[j];
+        for (int j = 0; j < kMaxQ; ++j) jp->nonlocal[j] = rp.nonlocal[j];
+        jp->n_events = (int)rp.ev_site.size();
+        const uint4* w = prog.data() + pi.words_begin;
+        const DevPhase* phs = reinterpret_cast<const DevPhase*>(w);
+        jp->phases.assign(phs, phs + pi.n_phases);
+        const OpRec* ops = reinterpret_cast<const OpRec*>(w + pi.ops_word);
+        jp->ops.assign(ops, ops + (pi.mats_word - pi.ops_word));
+        const float2* mts = reinterpret_cast<const float2*>(w + pi.mats_word);
+        jp->mats.assign(mts, mts + 2 * (pi.n_words - pi.mats_word));
+        todo.push_back(jp.get());
+        own.push_back(std::move(jp));
+    }
+    std::string err;
+    if (jit_compile(todo, &err) != 0) {
+        std::fprintf(stderr, "nqs jit: %s\n", err.c_str());
+        return NQS_ERR_COMPILE;
+    }
+    *compiled = (int)todo.size();
+    return NQS_OK;
+}
+
 int engine_jit_info(const Handle& h, int* state) {
     *state = (h.eng && h.eng->level >= 0) ? h.eng->jit_state : 0;
     return (h.eng && h.eng->level >= 0) ? h.eng->jit_launches : 0;

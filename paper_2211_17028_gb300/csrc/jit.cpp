@@ -968,6 +968,8 @@ struct Gen {
             o << "    const bool ok = mbar_wait(&bar[0], parity);\n";
             o << "    if (__syncthreads_or(!ok)) { failed = true; break; }\n";
             o << "    parity ^= 1u;\n";
+            // every state of the tile is in registers: phi is read once per tile
+            if (J.hint) o << "    const u64 polphi = pol_ef;\n    (void)polphi;\n";
             // load phase 0 from the staging buffer
             set_phase(0);
             for (int s = 0; s < S; ++s)
@@ -1193,7 +1195,7 @@ bool jit_available() { return nvrtc().ok; }
 
 long long jit_compile_count() { return g_compiles.load(); }
 
-int jit_build(std::vector<JitPass*>& passes, std::string* error) {
+int jit_compile(std::vector<JitPass*>& passes, std::string* error) {
     // distinct sources, compiled in parallel
     std::vector<std::pair<std::string, CacheEntry*>> todo;
     {
@@ -1232,6 +1234,12 @@ int jit_build(std::vector<JitPass*>& passes, std::string* error) {
             return -1;
         }
     }
+    return 0;
+}
+
+int jit_build(std::vector<JitPass*>& passes, std::string* error) {
+    if (jit_compile(passes, error) != 0) return -1;
+    std::lock_guard<std::mutex> g(g_cache_mu);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         if (error) *error = "no CUDA device";

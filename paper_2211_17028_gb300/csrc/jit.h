@@ -50,6 +50,8 @@ long long jit_compile_count();
 // Generate, compile (distinct sources in parallel, cached for the process)
 // and load every pass; 0 on success, -1 with a message otherwise.
 int jit_build(std::vector<JitPass*>& passes, std::string* error);
+// Generate and compile only (no device needed); 0 when every pass compiled.
+int jit_compile(std::vector<JitPass*>& passes, std::string* error);
 cudaError_t jit_launch(const JitPass& p, int grid, const PassArgs& a, cudaStream_t st);
 
 }  // namespace nqs

@@ -195,6 +195,8 @@ uint64_t engine_workspace_bytes(const Handle& h);
 uint64_t engine_upload_bytes(const Handle& h);
 uint64_t engine_launches_per_call(const Handle& h);
 int engine_jit_info(const Handle& h, int* state);
+// generate and compile (no device) the kernels of a forward sweep's first passes
+int engine_jit_compile_check(Handle& h, int states, int max_passes, int* compiled);
 // bounded-wait self-test (kernels_sweep.cu): status word into `status` (device)
 int selftest_bounded_wait(int* status, void* stream);
 int engine_reduced_matrix(const void* phi, const void* chi, int n, int qubit, double* R_out,

@@ -24,6 +24,7 @@ NQS_ERR_ORDER = 7
 NQS_ERR_DEVICE_TIMEOUT = 8
 NQS_ERR_UNSUPPORTED = 9
 NQS_ERR_TOO_LARGE = 10
+NQS_ERR_COMPILE = 11
 NQS_NOALLOC_MAX_QUBITS = 34
 
 NQS_STATE_BASIS = 0
@@ -119,6 +120,7 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_size_t)]),
     "nqs_truncation_bound": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "nqs_plan_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "nqs_jit_compile_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "nqs_shard_mask": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "nqs_general_factors": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32),
@@ -357,6 +359,13 @@ def nqs_plan_check(h):
     circuit's (host only, n <= 10)."""
     out = ctypes.c_double()
     _check(_lib().nqs_plan_check(h, ctypes.byref(out)), "nqs_plan_check")
+    return out.value
+
+
+def nqs_jit_compile_check(h, states, max_passes):
+    """Number of pass-specialised kernels generated and compiled (no device)."""
+    out = ctypes.c_int()
+    _check(_lib().nqs_jit_compile_check(h, states, max_passes, ctypes.byref(out)), "nqs_jit_compile_check")
     return out.value
 
 

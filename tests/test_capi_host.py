@@ -253,3 +253,53 @@ def test_general_factors_rebuild_the_noise_matrix():
         nqs.nqs_noise_factors(h, 0)
     assert e.value.code == nqs.NQS_ERR_UNSUPPORTED
     nqs.nqs_destroy(h)
+
+
+JIT_CIRCUITS = [
+    ("qaoa16", lambda: W.qaoa_workload(16, 3, 12, 3, "ideal", "qaoa16")),
+    ("random14", lambda: W.random_circuit(42, 14, 80, 5, v_kind="dense")),
+    ("grid15_ad_pd", lambda: W.random_circuit(43, 15, 120, 8, noise_kinds=("ad", "pd", "adpd"), v_kind="ideal")),
+]
+
+
+def _compile_check(make, states, passes=6):
+    h = _handle(make())
+    try:
+        return nqs.nqs_jit_compile_check(h, states, passes)
+    except nqs.NqsError as e:
+        if e.code == nqs.NQS_ERR_UNSUPPORTED:
+            pytest.skip("NVRTC not available")
+        raise
+    finally:
+        nqs.nqs_destroy(h)
+
+
+@pytest.mark.parametrize("states", [1, 3])
+@pytest.mark.parametrize("name,make", JIT_CIRCUITS, ids=[c[0] for c in JIT_CIRCUITS])
+def test_generated_kernels_compile(name, make, states):
+    # generator output of real passes (dense and diagonal gates on register,
+    # lane and tile-base qubits, reductions, spawns) compiles for sm_103a
+    assert _compile_check(make, states) >= 1
+
+
+@pytest.mark.parametrize("env", [{"NQS_JIT_SEQ": "0"}, {"NQS_JIT_RV": "1"}, {"NQS_JIT_HINT": "0"},
+                                 {"NQS_JIT_PP": "0"}, {"NQS_JIT_DB": "2"}, {"NQS_JIT_EARLY_PHI": "2"}],
+                         ids=["seq0", "rv1", "hint0", "pp0", "db2", "early2"])
+def test_generated_kernel_variants_compile(env, monkeypatch):
+    # the non-default forms of the generator (kept for comparison runs) still compile
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    assert _compile_check(JIT_CIRCUITS[0][1], 3, 4) >= 1
+    assert _compile_check(JIT_CIRCUITS[0][1], 1, 4) >= 1
+
+
+def test_compile_check_needs_a_prepared_wide_circuit():
+    h = nqs.nqs_load_circuit(W.to_ir_text(W.c1_line6()))
+    with pytest.raises(nqs.NqsError) as e:
+        nqs.nqs_jit_compile_check(h, 1, 1)
+    assert e.value.code == nqs.NQS_ERR_ORDER
+    nqs.nqs_prepare_noise(h, None, 0)
+    with pytest.raises(nqs.NqsError) as e:
+        nqs.nqs_jit_compile_check(h, 1, 1)   # 6 qubits: no generated kernels
+    assert e.value.code == nqs.NQS_ERR_UNSUPPORTED
+    nqs.nqs_destroy(h)
