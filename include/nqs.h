@@ -200,7 +200,8 @@ int nqs_plan_check(nqs_handle h, double* max_abs_err);
 /* Compile check of the pass-specialised kernels (host only, test hook; no
  * counterpart in the paper): the kernels of the first `max_passes` passes of
  * a forward sweep of the handle's plan over `states` states (1 or 3; with
- * reductions at every site and, for one state, spawns) are generated with the
+ * reductions and spawns at every site) and, for one state, of a backward
+ * sweep (adjoint operations, checkpoint saves) are generated with the
  * library's current settings and compiled with NVRTC for sm_103a; nothing is
  * loaded or run.  *compiled receives the number of kernels compiled.
  * Errors: NQS_ERR_ARG, NQS_ERR_ORDER (not prepared), NQS_ERR_UNSUPPORTED

@@ -1282,11 +1282,16 @@ int engine_jit_compile_check(Handle& h, int states, int max_passes, int* compile
     Tables tab;
     std::vector<DevOp> dops;
     std::vector<uint4> prog;
-    const Run run = make_run(plan, plan.free_passes, RT_FWD, true, states == 1, false, h.factors, tab, dops);
+    // forward passes with reductions and spawns at the sites; for one state also
+    // backward passes (adjoint operations, checkpoint saves)
+    std::vector<Run> runs;
+    runs.push_back(make_run(plan, plan.free_passes, RT_FWD, true, true, false, h.factors, tab, dops));
+    if (states == 1) runs.push_back(make_run(plan, plan.free_passes, RT_BWD, false, false, false, h.factors, tab, dops));
     std::vector<std::unique_ptr<JitPass>> own;
     std::vector<JitPass*> todo;
-    for (const RunPass& rp : run.passes) {
-        if ((int)todo.size() >= max_passes) break;
+    for (const Run& run : runs)
+    for (size_t ip = 0; ip < run.passes.size() && (int)ip < max_passes; ++ip) {
+        const RunPass& rp = run.passes[ip];
         const ProgInfo pi = build_program(dops, rp.op_off, rp.n_ops, 4, tab, prog, plan.k);
         std::unique_ptr<JitPass> jp(new JitPass());
         jp->S = states;
