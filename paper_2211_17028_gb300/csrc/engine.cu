@@ -1277,8 +1277,11 @@ int engine_launch_list(const Handle& h, nqs_launch_info* out, size_t cap, size_t
 
 int engine_jit_compile_check(Handle& h, int states, int max_passes, int* compiled) {
     *compiled = 0;
-    const Plan& plan = h.plan;
-    if (plan.k != kMaxTileQ || !jit_available()) return NQS_ERR_UNSUPPORTED;
+    if (h.plan.k != kMaxTileQ || !jit_available()) return NQS_ERR_UNSUPPORTED;
+    Plan wide;   // NQS_JIT_WIDE=1: the 13-qubit-tile form
+    const bool use_wide = jit_wide_enabled() && h.plan.n > kWideTileQ;
+    if (use_wide) make_wide_plan(h, wide);
+    const Plan& plan = use_wide ? wide : h.plan;
     Tables tab;
     std::vector<DevOp> dops;
     std::vector<uint4> prog;

@@ -283,8 +283,9 @@ def test_generated_kernels_compile(name, make, states):
 
 
 @pytest.mark.parametrize("env", [{"NQS_JIT_SEQ": "0"}, {"NQS_JIT_RV": "1"}, {"NQS_JIT_HINT": "0"},
-                                 {"NQS_JIT_PP": "0"}, {"NQS_JIT_DB": "2"}, {"NQS_JIT_EARLY_PHI": "2"}],
-                         ids=["seq0", "rv1", "hint0", "pp0", "db2", "early2"])
+                                 {"NQS_JIT_PP": "0"}, {"NQS_JIT_DB": "2"}, {"NQS_JIT_EARLY_PHI": "2"},
+                                 {"NQS_JIT_WIDE": "1"}],
+                         ids=["seq0", "rv1", "hint0", "pp0", "db2", "early2", "wide"])
 def test_generated_kernel_variants_compile(env, monkeypatch):
     # the non-default forms of the generator (kept for comparison runs) still compile
     for k, v in env.items():
