@@ -124,7 +124,10 @@ def fp32_roofline(launches, stats, n, multi, sm_mhz):
     peak = FP32_LANES * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "flops_per_launch": flops / len(sel),
-            "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x sampled SM clock (FMA peak)"}
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x sampled SM clock (FMA peak)",
+            "note": "algorithmic flops count every dense gate as a general complex matrix and every diagonal "
+                    "as a complex product; the generated kernels fold diagonals and drop zero parts, so they "
+                    "execute fewer"}
 
 
 def measured_peaks():
