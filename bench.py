@@ -560,7 +560,7 @@ def kernel_source_sha(jit=False):
     """Hash of the source that defines the timed sweep kernel: the pass
     generator when pass-specialised kernels ran, else the interpreting kernel."""
     import hashlib
-    p = os.path.join(ROOT, "paper_2211_17028_gb300", "csrc", "jit.cpp" if jit else "kernels_sweep.cu")
+    p = os.path.join(ROOT, "paper_2211_17028_gb300", "csrc", "jit.cpp" if jit else "kernels_sweep_body.cuh")
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 

@@ -47,6 +47,9 @@ def _compile(src, extra):
         return obj
     cmd = [nvcc(), "-c", src, "-o", obj, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
            "-Xcompiler", "-O2", "--expt-relaxed-constexpr"] + ARCH
+    if os.path.basename(src).startswith("kernels_sweep_s"):
+        # one kernel pair per unit: below nvcc's default compression threshold
+        cmd.append("--compress-mode=size")
     if extra.get("verbose_ptxas") and src.endswith(".cu"):
         cmd.append("-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

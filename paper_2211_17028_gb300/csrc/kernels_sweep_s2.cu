@@ -1,0 +1,10 @@
+// Instantiation of the register-resident sweep kernels (kernels_sweep_body.cuh)
+// for 2 states with 3 register qubits and 2 states with 4 register qubits, in a translation unit of its own so that the pairs compile in parallel.
+#include "kernels_sweep_body.cuh"
+
+namespace nqs {
+
+NQS_SWEEP_PAIR(2, 3)
+NQS_SWEEP_PAIR(2, 4)
+
+}  // namespace nqs
