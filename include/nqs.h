@@ -190,11 +190,15 @@ int nqs_truncation_bound(nqs_handle h, int level, double* out);
  * difference between the operator of the plan's operation order (fused
  * gates, the Hadamard-diagonal rewrite, the reordering before segmentation,
  * K_0 at the noise sites) and the operator of the circuit itself with K_0
- * after each noise's gate, both applied to every basis state in FP64
- * (+infinity when the plan does not keep the noise sites in their order).  No
- * counterpart in the paper (the plan is this library's).  n <= 10.
- * Errors: NQS_ERR_ARG, NQS_ERR_ORDER (not prepared), NQS_ERR_UNSUPPORTED
- * (general noises), NQS_ERR_TOO_LARGE (n > 10). */
+ * after each noise's gate, both applied to every basis state in FP64 (for
+ * n <= 10; 0 above).  +infinity when the plan's structure is broken: noise
+ * sites out of their order, or a pass (of the free or the site-cut
+ * segmentation) that does not continue where the previous one ended, whose
+ * tile is not k distinct ascending qubits holding the low qubits and every
+ * dense or site qubit of its operations, or that exceeds the operation or
+ * site bounds of a pass.  No counterpart in the paper (the plan is this
+ * library's).  Errors: NQS_ERR_ARG, NQS_ERR_ORDER (not prepared),
+ * NQS_ERR_UNSUPPORTED (general noises). */
 int nqs_plan_check(nqs_handle h, double* max_abs_err);
 
 /* Compile check of the pass-specialised kernels (host only, test hook; no

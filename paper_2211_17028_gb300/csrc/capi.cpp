@@ -323,11 +323,38 @@ int nqs_plan_check(nqs_handle hh, double* max_abs_err) {
     if (!h || !max_abs_err) return NQS_ERR_ARG;
     if (!h->prepared) return NQS_ERR_ORDER;
     if (h->general) return NQS_ERR_UNSUPPORTED;
-    if (h->circ.n > 10) return NQS_ERR_TOO_LARGE;
-    *max_abs_err = plan_product_error(h->circ, h->factors, h->plan);
+    const Plan& p = h->plan;
+    *max_abs_err = p.n <= 10 ? plan_product_error(h->circ, h->factors, p) : 0.0;
     // the sweeps take the noise sites in their order: site_pos must increase
-    for (size_t s = 1; s < h->plan.site_pos.size(); ++s)
-        if (h->plan.site_pos[s] <= h->plan.site_pos[s - 1]) *max_abs_err = HUGE_VAL;
+    for (size_t s = 1; s < p.site_pos.size(); ++s)
+        if (p.site_pos[s] <= p.site_pos[s - 1]) *max_abs_err = HUGE_VAL;
+    // pass structure of both segmentations
+    const int max_sites = h->opt_max_sites > 0 ? h->opt_max_sites : 4;
+    const int max_ops = h->opt_max_ops > 0 ? h->opt_max_ops : 96;
+    for (const std::vector<PassSpec>* segs : {&p.free_passes, &p.sitecut_passes}) {
+        int at = 0;
+        for (const PassSpec& ps : *segs) {
+            bool ok = ps.op_begin == at && ps.op_end > ps.op_begin && ps.op_end - ps.op_begin <= max_ops &&
+                      (int)ps.local.size() == p.k;
+            std::vector<char> in(p.n, 0);
+            for (size_t j = 0; j < ps.local.size() && ok; ++j) {
+                const int q = ps.local[j];
+                ok = q >= 0 && q < p.n && !in[q] && (j == 0 || q > ps.local[j - 1]);
+                if (ok) in[q] = 1;
+            }
+            for (int q = 0; q < p.c && ok; ++q) ok = in[q];
+            int sites = 0;
+            for (int i = ps.op_begin; i < ps.op_end && ok; ++i) {
+                const HostOp& o = p.ops[i];
+                if (o.type == OP_SITE) ++sites;
+                if (o.type == OP_G1 || o.type == OP_SITE) ok = in[o.q0];
+                if (o.type == OP_G2) ok = in[o.q0] && in[o.q1];
+            }
+            if (!ok || sites > max_sites) *max_abs_err = HUGE_VAL;
+            at = ps.op_end;
+        }
+        if (at != (int)p.ops.size()) *max_abs_err = HUGE_VAL;
+    }
     return NQS_OK;
 }
 

@@ -192,9 +192,22 @@ def test_plan_reordering_cuts_passes():
     # hoisting commuting operations into passes whose tiles are chosen for them
     h = _handle(W.c3_qaoa30())
     assert nqs.nqs_get_info(h)["n_passes"] <= 12
-    with pytest.raises(nqs.NqsError) as e:
-        nqs.nqs_plan_check(h)
-    assert e.value.code == nqs.NQS_ERR_TOO_LARGE
+    assert nqs.nqs_plan_check(h) == 0.0      # n > 10: the pass structure only
+    nqs.nqs_destroy(h)
+
+
+@pytest.mark.parametrize("make", [lambda: W.c2_grid20(), lambda: W.c5_twin_hot(), lambda: W.c5_grid(),
+                                  lambda: W.qaoa_workload(24, 3, 20, 4, "ideal", "qaoa24")],
+                         ids=["grid20", "twin20", "c5_28", "qaoa24"])
+def test_plan_structure_of_wide_circuits(make):
+    # every pass continues the previous one, holds its operations' dense and
+    # site qubits in a 12-qubit tile with the low qubits, and keeps the bounds
+    h = _handle(make())
+    assert nqs.nqs_plan_check(h) == 0.0
+    for ops, sites in ((64, 2), (160, 8)):
+        nqs.nqs_set_option(h, nqs.NQS_OPT_MAX_OPS, ops)
+        nqs.nqs_set_option(h, nqs.NQS_OPT_MAX_SITES, sites)
+        assert nqs.nqs_plan_check(h) == 0.0
     nqs.nqs_destroy(h)
 
 
