@@ -103,7 +103,7 @@ def make_workload(name):
 FP32_LANES = 152 * 128
 
 
-def fp32_roofline(launches, stats, n, multi, sm_mhz):
+def fp32_roofline(launches, stats, n, multi, sm_mhz, hbm_gbs=None):
     """Algorithmic FP32 flops of the dominant sweep launches over their time,
     against the FP32 FMA peak at the sampled SM clock.  Flops per amplitude of
     every swept state: 16 per dense one-qubit gate (two complex multiply-adds),
@@ -115,19 +115,27 @@ def fp32_roofline(launches, stats, n, multi, sm_mhz):
     if not sel or not stats["total_ms"]:
         return None
     dim = float(2 ** n)
+    peak = FP32_LANES * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
     flops = 0.0
+    bound_s = 0.0    # per launch the larger of its memory time and its FP32 time at the peaks
     for l in sel:
         per_amp = 16 * l["g1"] + 32 * l["g2"] + 6 * (l["d1"] + l["d2"]) + 16 * l["reductions"]
-        flops += dim * (l["states"] * per_amp + 16 * l["spawned"])
+        f = dim * (l["states"] * per_amp + 16 * l["spawned"])
+        flops += f
+        if hbm_gbs:
+            bound_s += max(l.get("algorithmic_bytes", 0.0) / (hbm_gbs * 1e9), f / (peak * 1e12))
     calls = stats["launches"] / len(sel)
     achieved = flops * calls / (stats["total_ms"] / 1000.0) / 1e12
-    peak = FP32_LANES * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "flops_per_launch": flops / len(sel),
-            "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x sampled SM clock (FMA peak)",
-            "note": "algorithmic flops count every dense gate as a general complex matrix and every diagonal "
-                    "as a complex product; the generated kernels fold diagonals and drop zero parts, so they "
-                    "execute fewer"}
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+           "flops_per_launch": flops / len(sel),
+           "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x sampled SM clock (FMA peak)",
+           "note": "algorithmic flops count every dense gate as a general complex matrix and every diagonal "
+                   "as a complex product; the generated kernels fold diagonals and drop zero parts, so they "
+                   "execute fewer"}
+    if hbm_gbs:
+        # the launches' time if each ran at the larger of its two bounds, over the measured time
+        out["combined_bound_frac"] = bound_s * calls / (stats["total_ms"] / 1000.0)
+    return out
 
 
 def measured_peaks():
@@ -467,7 +475,8 @@ def run_nqs(args):
         with open(args.launch_list, "w") as f:
             json.dump(launch_list, f)
     try:   # the same launches against the FP32 arithmetic peak (near the ridge point)
-        roof_fp32 = fp32_roofline(launch_list, dom, w.n, dom is multi, clk.get("sm_mhz")) if launch_list else None
+        roof_fp32 = (fp32_roofline(launch_list, dom, w.n, dom is multi, clk.get("sm_mhz"), peak)
+                     if launch_list else None)
     except Exception as ex:  # never sink the main measurement
         roof_fp32 = {"failed": str(ex)}
     # end to end through the public API from host data (the timed handle's
