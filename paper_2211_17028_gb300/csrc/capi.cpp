@@ -500,7 +500,11 @@ namespace {
 void resegment(Handle& h) {
     const int sites = h.opt_max_sites > 0 ? h.opt_max_sites : 4;
     const int ops = h.opt_max_ops > 0 ? h.opt_max_ops : 96;
-    h.plan.free_passes = segment(h.plan, false, sites, ops);
+    // the reordering's passes keep any bounds at least as loose as their own
+    if (!h.plan.grouped_passes.empty() && sites >= 4 && ops >= 96)
+        h.plan.free_passes = h.plan.grouped_passes;
+    else
+        h.plan.free_passes = segment(h.plan, false, sites, ops);
     h.plan.sitecut_passes = segment(h.plan, true, sites, ops);
 }
 

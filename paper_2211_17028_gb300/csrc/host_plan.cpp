@@ -325,10 +325,12 @@ void build_plan(const Circuit& c, const std::vector<Factors>& f, int tile_qubits
     // program and reduction slots fit next to the tiles in shared memory
     {
         const char* e = std::getenv("NQS_PLAN_REORDER");   // 0: keep the circuit order
-        if (!(e && e[0] == '0'))
-            lookahead_order(p, 4, 96, p.free_passes);
-        else
+        if (!(e && e[0] == '0')) {
+            lookahead_order(p, 4, 96, p.grouped_passes);
+            p.free_passes = p.grouped_passes;
+        } else {
             p.free_passes = segment(p, false, 4, 96);
+        }
     }
     p.sitecut_passes = segment(p, true, 4, 96);
 }

@@ -103,6 +103,7 @@ struct Plan {
     std::vector<int> site_pos;     // op index of each site's OP_SITE
     std::vector<PassSpec> free_passes;     // cuts only where locality forces them
     std::vector<PassSpec> sitecut_passes;  // additionally cut after every OP_SITE
+    std::vector<PassSpec> grouped_passes;  // the reordering's own passes (at most 4 sites, 96 operations)
 };
 
 void build_plan(const Circuit& c, const std::vector<Factors>& f, int tile_qubits, Plan& out);

@@ -193,6 +193,12 @@ def test_plan_reordering_cuts_passes():
     h = _handle(W.c3_qaoa30())
     assert nqs.nqs_get_info(h)["n_passes"] <= 12
     assert nqs.nqs_plan_check(h) == 0.0      # n > 10: the pass structure only
+    # looser segmentation bounds keep the reordering's passes, tighter ones cut in order
+    nqs.nqs_set_option(h, nqs.NQS_OPT_MAX_OPS, 128)
+    nqs.nqs_set_option(h, nqs.NQS_OPT_MAX_SITES, 8)
+    assert nqs.nqs_get_info(h)["n_passes"] <= 12
+    nqs.nqs_set_option(h, nqs.NQS_OPT_MAX_OPS, 64)
+    assert nqs.nqs_get_info(h)["n_passes"] > 12 and nqs.nqs_plan_check(h) == 0.0
     nqs.nqs_destroy(h)
 
 
