@@ -198,6 +198,7 @@ def test_plan_reordering_cuts_passes():
     nqs.nqs_set_option(h, nqs.NQS_OPT_MAX_SITES, 8)
     assert nqs.nqs_get_info(h)["n_passes"] <= 12
     nqs.nqs_set_option(h, nqs.NQS_OPT_MAX_OPS, 64)
+    nqs.nqs_set_option(h, nqs.NQS_OPT_MAX_SITES, 2)
     assert nqs.nqs_get_info(h)["n_passes"] > 12 and nqs.nqs_plan_check(h) == 0.0
     nqs.nqs_destroy(h)
 
